@@ -1,0 +1,366 @@
+"""Benchmark of the stencil hot path on the 512^3 constant-coefficient workload.
+
+Workload (one "step"): on a 512^3 f32 periodic grid with uniform[-1,1] input,
+  (a) the 25-point radius-4 star with 8th-order Laplacian weights, 1 sweep and 8 sweeps;
+  (b) the 27-point 3x3x3 box with seeded weights normalised to sum 1, 1 sweep and 8 sweeps;
+18 sweeps = 18 * 512^3 cell updates.  Metric: Gcell-updates/s (higher is better).
+
+Inputs are 512 MiB per array (larger than the 129 MB L2), so no L2 flush is needed between
+timed iterations.  Timing: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), measured with CUDA events on the launching stream; the maximum over
+ranks is taken.  Several GPUs run independent replicas (weak scaling, no collective).
+
+--impl reference times the FP64 oracle (single-threaded C) on the host on a bounded sample
+of the same workload; that is this project's reference arm.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 512
+CELLS = N ** 3
+SWEEPS_PER_STEP = 1 + 8 + 1 + 8
+ALG_BYTES_PER_CELL = 8  # f32: read one value, write one value per cell and sweep
+METRIC = "Gcell-updates/s"
+WORKLOAD = "3D const-coefficient sweeps 512^3 f32 periodic: 25-pt star r4 (8th-order " \
+           "Laplacian) and 27-pt box (weights sum 1), 1 and 8 steps each"
+
+
+def rank_info():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", str(r)))
+    return r, w, lr
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(device):
+    """Plans and device-resident inputs/outputs of the four sub-workloads."""
+    import torch
+
+    import paper_2609_06694_gb300 as gs
+    from paper_2609_06694_gb300 import inputs
+
+    dims = (N, N, N)
+    star = gs.stencil_plan(3, dims, "star", 4, "const", np.ones(25), "f32", "periodic")
+    offs_s = gs.stencil_offsets(star)
+    c_star = inputs.laplacian_coeffs(offs_s, 4)
+    star = gs.stencil_plan(3, dims, "star", 4, "const", c_star, "f32", "periodic")
+    c_box, _ = inputs.normalised_sum_weights(2002, 27)
+    box = gs.stencil_plan(3, dims, "box", 1, "const", c_box, "f32", "periodic")
+    x_star = inputs.to_storage(inputs.uniform(2001, dims), "f32")
+    x_box = inputs.to_storage(inputs.uniform(2003, dims), "f32")
+    return {"star": star, "box": box, "x_star_host": x_star, "x_box_host": x_box,
+            "x_star": x_star.to(device), "x_box": x_box.to(device),
+            "y": torch.empty(dims, dtype=torch.float32, device=device),
+            "c_star": c_star, "c_box": c_box, "offs_star": offs_s}
+
+
+def run_step(gs, W, stream, ev=None):
+    """The 18 sweeps; with ev, records events around each call: [(name, launches, s, e)]."""
+    import torch
+    calls = (("star", "x_star", 1), ("star", "x_star", 8), ("box", "x_box", 1),
+             ("box", "x_box", 8))
+    for name, xin, steps in calls:
+        if ev is not None:
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+        gs.stencil_apply(W[name], W[xin], W["y"], steps, stream=stream)
+        if ev is not None:
+            e.record(stream)
+            ev.append((name, steps, s, e))
+
+
+def traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    src = os.path.join(ROOT, "paper_2609_06694_gb300", "csrc", "stream.cuh")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for ln in text.splitlines():
+            if ln.startswith("- ") and ":" in ln:
+                k, v = ln[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+        if vals.get("stream.cuh sha256[:16]") != sha:
+            return None
+        return float(vals["dram bytes per launch"])
+    except Exception:
+        return None
+
+
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, lrank = rank_info()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(lrank)
+    device = torch.device("cuda", lrank)
+    from paper_2609_06694_gb300 import build
+    build.build()
+    import paper_2609_06694_gb300 as gs
+
+    W = build_workload(device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        run_step(gs, W, stream)
+    torch.cuda.synchronize()
+    for name in ("star", "box"):
+        rc = gs.stencil_sync_status(W[name])
+        if rc != 0:
+            raise RuntimeError(f"kernel error {rc}")
+
+    sampler = ClockSampler(lrank)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = gs.stencil_launch_count()
+    ev = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        run_step(gs, W, stream, ev)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = gs.stencil_launch_count() - launches0
+    clocks = sampler.stop()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    updates = SWEEPS_PER_STEP * CELLS * args.steps * world
+    value = updates / (ms_total * 1e-3) / 1e9
+
+    # per-kernel timing from the events: star r4 sweep kernel is the dominant kernel
+    per = {"star": [0.0, 0], "box": [0.0, 0]}
+    for name, steps, s, e in ev:
+        per[name][0] += s.elapsed_time(e)
+        per[name][1] += steps
+    dom = max(per, key=lambda k: per[k][0])
+    ms_launch = per[dom][0] / per[dom][1]
+    peak, peak_src = measured_peaks()
+    achieved = ALG_BYTES_PER_CELL * CELLS / (ms_launch * 1e-3) / 1e9
+    tag = "stream_sweep_star_r4_512" if dom == "star" else "stream_sweep_box_r1_512"
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic_from_profile(tag),
+                "kernel": f"stream_sweep_kernel ({dom}), 1 sweep per launch",
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": ALG_BYTES_PER_CELL * CELLS,
+                "ms_per_launch": round(ms_launch, 4),
+                "per_kernel_ms_per_launch": {k: round(v[0] / v[1], 4) for k, v in per.items()}}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    xs = W["x_star_host"].pin_memory()
+    xb = W["x_box_host"].pin_memory()
+    yh = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        gs.stencil_apply_host(W["star"], xs, yh, 1, stream=stream)
+        gs.stencil_apply_host(W["star"], xs, yh, 8, stream=stream)
+        gs.stencil_apply_host(W["box"], xb, yh, 1, stream=stream)
+        gs.stencil_apply_host(W["box"], xb, yh, 8, stream=stream)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    h0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - h0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = SWEEPS_PER_STEP * CELLS * e2e_steps * world / e2e_s / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(W)
+
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N, N, N], "boundary": "periodic",
+                       "sweeps_per_step": SWEEPS_PER_STEP, "l2": "inputs 512 MiB > L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_val, 3), "unit": "Gcell-updates/s",
+                    "h2d_bytes_per_step": 4 * CELLS * 4, "d2h_bytes_per_step": 4 * CELLS * 4,
+                    "api": "stencil_apply_host (pinned host buffers)"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_sample(seed_star=2001, seed_box=2003, nz=16):
+    """One oracle sweep of each stencil on an nz x 512 x 512 periodic f64 grid; returns
+    (cell updates, seconds, description)."""
+    import oracle
+    from paper_2609_06694_gb300 import inputs
+    dims = (nz, N, N)
+    offs_s = oracle.offsets(3, "star", 4)
+    c_s = inputs.laplacian_coeffs(offs_s, 4)
+    offs_b = oracle.offsets(3, "box", 1)
+    c_b, _ = inputs.normalised_sum_weights(2002, 27)
+    xs = inputs.stored_values(inputs.to_storage(inputs.uniform(seed_star, dims), "f32"))
+    xb = inputs.stored_values(inputs.to_storage(inputs.uniform(seed_box, dims), "f32"))
+    t0 = time.perf_counter()
+    oracle.sweep_const(xs, offs_s, c_s, "periodic")
+    oracle.sweep_const(xb, offs_b, c_b, "periodic")
+    dt = time.perf_counter() - t0
+    desc = (f"one FP64 oracle sweep of the 25-pt star and of the 27-pt box on a {nz}x512x512 "
+            "periodic grid (same per-cell work as the 512^3 sweeps)")
+    return 2 * nz * N * N, dt, desc
+
+
+def cpu_baseline_sample(W=None):
+    updates, dt, desc = _oracle_sample(nz=96)
+    return {"value": round(updates / dt / 1e9, 6), "unit": "Gcell-updates/s", "cores": 1,
+            "kind": "oracle", "sample": desc, "seconds": round(dt, 2)}
+
+
+def bench_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        _oracle_sample(nz=2)
+    total_u, total_t = 0, 0.0
+    desc = None
+    for _ in range(args.steps):
+        u, dt, desc = _oracle_sample(nz=2)
+        total_u += u
+        total_t += dt
+    value = total_u / total_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6),
+        "unit": "Gcell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_t / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N, N, N], "boundary": "periodic",
+                   "sample": desc},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gcell-updates/s", "cores": 1,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(value, 6), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: at least 3 warm-up steps are required; using 3", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * GB300 stencil operator library -- C ABI.
+ *
+ * The library computes the stencil sweep of ForgeStencil Sec. 2.1,
+ *     u^{t+1}(p) = sum_{o in S} c_o u^t(p + o)            (constant coefficients), or
+ *     u^{t+1}(p) = sum_{o in S} w_o(p) u^t(p + o)         (coefficients that vary in space),
+ * for an offset set S of star, box or diamond type and order (radius) r = 1..4 on a 2D or 3D
+ * grid, iterated over time steps (Sec. 2.1; several steps may be fused into one launch,
+ * Sec. 4.3).  Values are stored as f32, f16 or bf16 and accumulated in f32.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: STENCIL_OK (0) or a negative STENCIL_ERR_* code.  No C++ exception
+ *    crosses this boundary.  stencil_strerror() names a code.
+ *  - Grids are dense and row-major: dims[] lists the extents slowest axis first ((nz, ny, nx)
+ *    in 3D, (ny, nx) in 2D) and the last axis is contiguous.  No padding.
+ *  - Offsets are written slowest axis first and enumerated in the canonical order:
+ *    lexicographic over (dz, dy, dx), each component from -r to r, restricted to the shape.
+ *    Star: one nonzero component at most; box: max |component| <= r; diamond: sum of
+ *    |component| <= r.  Coefficient arrays follow this order (stencil_offsets returns it).
+ *  - Boundaries: STENCIL_DIRICHLET0 updates every cell and reads 0 outside the grid;
+ *    STENCIL_PERIODIC wraps every read (index mod extent).
+ *  - Pointers named `in`, `out`, `coeff_arrays[i]` are DEVICE pointers owned by the caller.
+ *    `in` and `out` must not overlap.  Device buffers aligned to 16 bytes whose row length in
+ *    bytes is a multiple of 16 take the vectorised path; others take a scalar path (still on
+ *    the GPU, slower).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Launches
+ *    are asynchronous; argument errors are returned at once, CUDA launch errors as
+ *    STENCIL_ERR_CUDA, and errors detected by a kernel (a bounded wait that expired, an index
+ *    check) are latched in a device word read by stencil_sync_status / stencil_batch_status.
+ *  - A plan is not thread-safe: do not use one handle from two host threads at once.
+ */
+#ifndef GB300_STENCIL_H
+#define GB300_STENCIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define STENCIL_OK 0
+#define STENCIL_ERR_BADARG (-1)      /* invalid argument (null pointer, bad size, ...)       */
+#define STENCIL_ERR_UNSUPPORTED (-2) /* valid request this build has no kernel for          */
+#define STENCIL_ERR_OOM (-3)         /* device or host allocation failed                    */
+#define STENCIL_ERR_CUDA (-4)        /* a CUDA runtime call failed                           */
+#define STENCIL_ERR_TIMEOUT (-5)     /* a bounded device-side wait expired                   */
+#define STENCIL_ERR_BOUNDS (-6)      /* a device-side index check failed                     */
+
+/* ---- enumerations ------------------------------------------------------------------------ */
+#define STENCIL_STAR 0
+#define STENCIL_BOX 1
+#define STENCIL_DIAMOND 2
+
+#define STENCIL_F32 0
+#define STENCIL_F16 1
+#define STENCIL_BF16 2
+
+#define STENCIL_DIRICHLET0 0
+#define STENCIL_PERIODIC 1
+
+#define STENCIL_CONST 0    /* one coefficient per offset                                      */
+#define STENCIL_VAR 1      /* one coefficient array per offset, read at the output cell       */
+#define STENCIL_DIVKGRAD 2 /* div(k grad u), unit spacing, conservative star-1 form (below)   */
+
+typedef struct stencil_plan_s *stencil_handle;
+typedef struct stencil_batch_s *stencil_batch;
+
+/* ---- plans ------------------------------------------------------------------------------- */
+
+/* stencil_plan -- validate a stencil request and choose its kernel (Sec. 2.1: offset set,
+ * coefficients, grid and precision; Sec. 4.3: the kernel is specialised per stencil type,
+ * grid shape and precision).
+ *   out      receives the new handle (host memory owned by the library; free with
+ *            stencil_destroy).  The call allocates no device memory.
+ *   ndim     2 or 3; dims[ndim] extents, slowest first, each >= 1.
+ *   shape    STENCIL_STAR / BOX / DIAMOND; radius 1..4 (kind DIVKGRAD: star, radius 1).
+ *   kind     STENCIL_CONST: coeffs[ncoeffs] holds one weight per offset in canonical order
+ *            (ncoeffs must equal the offset count); the values are copied.
+ *            STENCIL_VAR / STENCIL_DIVKGRAD: coeffs must be NULL and ncoeffs 0; the arrays are
+ *            passed to stencil_apply_var.
+ *   dtype    storage type of every grid array (STENCIL_F32 / F16 / BF16).
+ *   boundary STENCIL_DIRICHLET0 or STENCIL_PERIODIC.
+ * Errors: BADARG for out-of-range values or a count mismatch; UNSUPPORTED for a combination
+ * without a kernel.  The kernel choice comes from the dispatch map (stencil_load_dispatch_map)
+ * or from built-in defaults. */
+int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, int radius,
+                 int kind, const double *coeffs, int64_t ncoeffs, int dtype, int boundary);
+
+/* stencil_offsets -- the plan's offsets in canonical order.  Writes min(n, capacity) rows of
+ * ndim int32 (slowest component first) to offsets_out (may be NULL when capacity is 0) and the
+ * full count to *n. */
+int stencil_offsets(stencil_handle h, int32_t *offsets_out, int64_t capacity, int64_t *n);
+
+/* stencil_destroy -- free a plan and any device scratch it allocated (synchronises the
+ * device before freeing).  NULL is accepted. */
+int stencil_destroy(stencil_handle h);
+
+/* ---- sweeps ------------------------------------------------------------------------------ */
+
+/* stencil_apply -- `steps` >= 1 sweeps of a STENCIL_CONST plan: out = A^steps in
+ * (Sec. 2.1 update rule iterated over t; fused groups of steps per launch as in Sec. 4.3).
+ * Between steps the values are rounded to the storage type (round to nearest even), also
+ * inside a fused launch, so the result does not depend on how steps are grouped.
+ * `in` is not modified.  steps > 1 ping-pongs through `out` and one grid-sized scratch buffer
+ * that the plan allocates on first use (cudaMalloc) and keeps until stencil_destroy. */
+int stencil_apply(stencil_handle h, const void *in, void *out, int steps, void *stream);
+
+/* stencil_apply_adjoint -- out = (A^T)^steps in for a STENCIL_CONST plan: the transposed sweep
+ * (A^T y)[q] = sum_o c_o y[q - o], i.e. the stencil with every offset flipped. */
+int stencil_apply_adjoint(stencil_handle h, const void *in, void *out, int steps, void *stream);
+
+/* stencil_apply_var -- sweeps of a STENCIL_VAR or STENCIL_DIVKGRAD plan.
+ *   VAR:      coeff_arrays[npts] are device pointers to grid-shaped arrays of the storage
+ *             type; out[p] = sum_o coeff_arrays[o][p] * in[p + o]  (Sec. 2.1).
+ *   DIVKGRAD: coeff_arrays[0] is k (grid-shaped, storage type, k > 0);
+ *             out[p] = sum_axes [ kf+ (u[p+e] - u[p]) - kf- (u[p] - u[p-e]) ],
+ *             kf+- = (k[p] + k[p+-e]) / 2; with STENCIL_DIRICHLET0, u reads 0 and k reads
+ *             k[p] outside the grid.  This operator is symmetric.
+ * `coeff_arrays` itself is a HOST array of device pointers. */
+int stencil_apply_var(stencil_handle h, const void *in, const void *const *coeff_arrays,
+                      void *out, int steps, void *stream);
+
+/* stencil_apply_adjoint_var -- the transpose of stencil_apply_var:
+ *   VAR:      out[q] = sum_o coeff_arrays[o][q - o] * in[q - o]  (offset flipped, coefficient
+ *             gathered at the shifted cell);
+ *   DIVKGRAD: the operator is symmetric, so this equals stencil_apply_var. */
+int stencil_apply_adjoint_var(stencil_handle h, const void *in,
+                              const void *const *coeff_arrays, void *out, int steps,
+                              void *stream);
+
+/* stencil_apply_host -- stencil_apply on HOST buffers: copies `in_host` to a device staging
+ * buffer, sweeps, and copies the result to `out_host`, all on `stream`, then synchronises the
+ * stream.  Pinned host memory gives full copy bandwidth.  The staging buffers are allocated
+ * on first use and kept by the plan. */
+int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, int steps,
+                       void *stream);
+
+/* stencil_sync_status -- synchronise `stream` and return the first error latched by a kernel
+ * of this plan since the last call (then clear it). */
+int stencil_sync_status(stencil_handle h, void *stream);
+
+/* ---- batched sweeps (many grids, one persistent launch) ---------------------------------- */
+
+typedef struct {
+    stencil_handle plan; /* a 2D STENCIL_CONST plan describing this grid                    */
+    const void *in;      /* device input, plan's dims and dtype                             */
+    void *out;           /* device output                                                    */
+} stencil_batch_item;
+
+/* stencil_batch_plan -- build a tile work list over `n` grids (2D, constant coefficients,
+ * any mix of shapes, radii <= 4, dtypes and sizes) for `steps` sweeps each, allocate the
+ * device scratch it needs, and capture one persistent cooperative kernel (plus the reset of
+ * its counters) into a CUDA graph.  Every step boundary is a device-wide barrier whose wait
+ * is bounded; an expired wait latches STENCIL_ERR_TIMEOUT.  The plans and buffers named by
+ * `items` must outlive the batch; the items array is copied. */
+int stencil_batch_plan(stencil_batch *out, const stencil_batch_item *items, int n, int steps);
+
+/* stencil_batch_launch -- launch the captured graph on `stream`. */
+int stencil_batch_launch(stencil_batch b, void *stream);
+
+/* stencil_batch_status -- synchronise `stream` and return the batch's latched device error. */
+int stencil_batch_status(stencil_batch b, void *stream);
+
+/* stencil_batch_destroy -- free the batch, its graph and its scratch. */
+int stencil_batch_destroy(stencil_batch b);
+
+/* ---- tuning and dispatch ----------------------------------------------------------------- */
+
+typedef struct {
+    int family;  /* kernel family chosen (STENCIL_FAMILY_*)                                     */
+    int block_x; /* threads along x                                                             */
+    int block_y; /* threads along y                                                             */
+    int vec_y;   /* rows per thread                                                             */
+    int z_chunk; /* planes per CTA (3D streaming); 0 = whole extent                             */
+    int fuse;    /* time steps fused per launch                                                 */
+    int tile_x;  /* output tile width of fused 2D kernels (0 = default)                         */
+    int tile_y;  /* output tile height of fused 2D kernels (0 = default)                        */
+} stencil_variant;
+
+#define STENCIL_FAMILY_STREAM 1 /* one sweep per launch, z-streaming tiles, cp.async pipeline  */
+#define STENCIL_FAMILY_FUSED2D 2 /* several 2D sweeps per launch in a shared-memory tile      */
+
+/* stencil_plan_get_variant / stencil_plan_set_variant -- read or override the kernel variant
+ * a plan uses (the autotuner's knob).  set validates the variant against the plan and returns
+ * BADARG or UNSUPPORTED without changing the plan when it cannot run. */
+int stencil_plan_get_variant(stencil_handle h, stencil_variant *v);
+int stencil_plan_set_variant(stencil_handle h, const stencil_variant *v);
+
+/* stencil_load_dispatch_map -- replace the process-wide dispatch map with the one in the
+ * text file at `path` (format: lines "ndim shape radius dtype boundary kind size_class :
+ * family block_x block_y vec_y z_chunk fuse tile_x tile_y", '#' comments).  Plans created
+ * afterwards use it.  NULL restores the built-in defaults. */
+int stencil_load_dispatch_map(const char *path);
+
+/* stencil_size_class -- the size class (0 .. 3) a grid of `cells` cells falls in. */
+int stencil_size_class(int64_t cells);
+
+/* ---- introspection ----------------------------------------------------------------------- */
+
+/* stencil_launch_count -- number of kernels this library has launched in the process. */
+uint64_t stencil_launch_count(void);
+
+/* stencil_strerror -- static string naming a status code. */
+const char *stencil_strerror(int code);
+
+/* stencil_abi_version -- ABI version of this header (STENCIL_ABI_VERSION). */
+#define STENCIL_ABI_VERSION 1
+int stencil_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_STENCIL_H */

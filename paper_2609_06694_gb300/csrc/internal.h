@@ -1,0 +1,65 @@
+// Internal interface between the host plan code (plan.cpp) and the kernel translation units.
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gst {
+
+// One launch of the streaming sweep kernel (one time step).
+struct StreamLaunch {
+    int ndim;                // 2 or 3
+    int64_t nz, ny, nx;      // 2D: nz = 1
+    int shape, radius, dtype;
+    int periodic;
+    const float *coeffs;     // host array, canonical order, shape_count entries
+    const void *in;
+    void *out;
+    int block_x, block_y, vec_y, z_chunk;
+    int *err;                // device error word or null
+    cudaStream_t stream;
+};
+
+// Returns 0, or a negative STENCIL_ERR_* code.  One per storage type and dimension.
+// Defined in stream_<dtype>_<ndim>d_<shape>.cu.
+#define GST_DECLARE_STREAM(DT, ND)                          \
+    int launch_stream_##DT##_##ND##d_star(const StreamLaunch &L); \
+    int launch_stream_##DT##_##ND##d_box(const StreamLaunch &L);  \
+    int launch_stream_##DT##_##ND##d_diamond(const StreamLaunch &L);
+GST_DECLARE_STREAM(f32, 2)
+GST_DECLARE_STREAM(f32, 3)
+GST_DECLARE_STREAM(f16, 2)
+GST_DECLARE_STREAM(f16, 3)
+GST_DECLARE_STREAM(bf16, 2)
+GST_DECLARE_STREAM(bf16, 3)
+#undef GST_DECLARE_STREAM
+int launch_stream(const StreamLaunch &L);  // dispatches on dtype, ndim and shape
+
+// Rows per thread compiled for a streaming kernel: 1 always; 2 for every 2D stencil, every 3D
+// star and 3D box/diamond up to radius 2 (wider 3D stencils are ALU-heavy enough that the
+// second row's registers cost more than the shared-memory reads they save).
+constexpr bool stream_vy_compiled(int ndim, int shape, int radius, int vec_y) {
+    return vec_y == 1 || (vec_y == 2 && (ndim == 2 || shape == 0 || radius <= 2));
+}
+
+// Several 2D time steps in one launch (shared-memory tile with a shrinking halo).
+struct Fused2DLaunch {
+    int64_t ny, nx;
+    int shape, radius, dtype;
+    int periodic;
+    const float *coeffs;     // host array, canonical order
+    const void *in;
+    void *out;
+    int steps;               // steps fused in this launch (>= 1)
+    int tile_x, tile_y;      // output tile
+    int block_threads;
+    cudaStream_t stream;
+};
+int launch_fused2d(const Fused2DLaunch &L);
+size_t fused2d_smem_bytes(int tile_x, int tile_y, int radius, int steps);
+
+// Kernel launch counter (all families).
+void count_launch(uint64_t n = 1);
+
+}  // namespace gst

@@ -1,0 +1,484 @@
+// Host side of the C ABI declared in include/stencil.h: plan validation, the dispatch map,
+// multi-step scheduling (ping-pong through a plan-owned scratch grid) and error reporting.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/stencil.h"
+#include "internal.h"
+#include "plan_internal.h"
+
+namespace gst {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------------------
+// Offset sets (canonical order: lexicographic (dz, dy, dx), each -r..r).
+// ---------------------------------------------------------------------------------------
+static bool host_in_shape(int ndim, int shape, int r, int dz, int dy, int dx) {
+    if (ndim == 2 && dz != 0) return false;
+    int az = std::abs(dz), ay = std::abs(dy), ax = std::abs(dx);
+    if (az > r || ay > r || ax > r) return false;
+    if (shape == STENCIL_STAR) return ((dz != 0) + (dy != 0) + (dx != 0)) <= 1;
+    if (shape == STENCIL_BOX) return true;
+    return az + ay + ax <= r;
+}
+
+std::vector<int32_t> make_offsets(int ndim, int shape, int r) {
+    std::vector<int32_t> out;
+    const int zr = ndim == 3 ? r : 0;
+    for (int dz = -zr; dz <= zr; ++dz)
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx)
+                if (host_in_shape(ndim, shape, r, dz, dy, dx)) {
+                    if (ndim == 3) out.push_back(dz);
+                    out.push_back(dy);
+                    out.push_back(dx);
+                }
+    return out;
+}
+
+// ---------------------------------------------------------------------------------------
+// Dispatch map
+// ---------------------------------------------------------------------------------------
+struct MapEntry {
+    int key[7];  // ndim shape radius dtype boundary kind size_class
+    stencil_variant v;
+};
+static std::mutex g_map_mu;
+static std::vector<MapEntry> g_map;
+
+int size_class_of(int64_t cells) {
+    if (cells < (int64_t)1 << 16) return 0;
+    if (cells < (int64_t)1 << 20) return 1;
+    if (cells < (int64_t)1 << 24) return 2;
+    return 3;
+}
+
+// Built-in defaults (used when the map has no entry for a key).
+static stencil_variant default_variant(const stencil_plan_s &p) {
+    stencil_variant v;
+    std::memset(&v, 0, sizeof(v));
+    const int es = p.dtype == STENCIL_F32 ? 4 : 2;
+    const int vx = 16 / es;
+    v.family = STENCIL_FAMILY_STREAM;
+    v.block_x = 128 / vx;  // 128-cell tiles in x
+    v.block_y = 256 / v.block_x;
+    v.vec_y = 1;
+    v.z_chunk = p.ndim == 3 ? 64 : 0;
+    v.fuse = 1;
+    if (p.ndim == 3) {
+        // two rows per thread while the partial-sum queue stays small
+        if (stream_vy_compiled(3, p.shape, p.radius, 2) && p.radius <= 2) {
+            v.vec_y = 2;
+            v.block_y /= 2;
+        }
+    } else {
+        v.vec_y = 2;
+        v.block_y = 4;
+        const int64_t cells = p.dims[1] * p.dims[2];
+        if (cells <= ((int64_t)1 << 20)) {
+            v.family = STENCIL_FAMILY_FUSED2D;
+            v.fuse = 8;
+            v.tile_x = 32;
+            v.tile_y = 32;
+            v.block_x = 256;
+            v.block_y = 1;
+            v.vec_y = 1;
+        }
+    }
+    return v;
+}
+
+static bool lookup_map(const stencil_plan_s &p, stencil_variant *out) {
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    const int key[7] = {p.ndim, p.shape, p.radius, p.dtype, p.boundary, p.kind,
+                        size_class_of(p.dims[0] * p.dims[1] * p.dims[2])};
+    for (const MapEntry &e : g_map) {
+        bool ok = true;
+        for (int i = 0; i < 7; ++i)
+            if (e.key[i] != key[i] && e.key[i] != -1) ok = false;
+        if (ok) {
+            *out = e.v;
+            return true;
+        }
+    }
+    return false;
+}
+
+int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
+    if (v.family == STENCIL_FAMILY_STREAM) {
+        if (v.block_x < 1 || v.block_y < 1 || v.block_x * v.block_y > 256 ||
+            (v.block_x * v.block_y) % 32 != 0)
+            return STENCIL_ERR_BADARG;
+        if (!stream_vy_compiled(p.ndim, p.shape, p.radius, v.vec_y))
+            return STENCIL_ERR_UNSUPPORTED;
+        if (v.z_chunk < 0 || v.fuse != 1) return STENCIL_ERR_BADARG;
+        return STENCIL_OK;
+    }
+    if (v.family == STENCIL_FAMILY_FUSED2D) {
+        if (p.ndim != 2) return STENCIL_ERR_UNSUPPORTED;
+        if (v.fuse < 1 || v.tile_x < 1 || v.tile_y < 1) return STENCIL_ERR_BADARG;
+        if (v.block_x < 32 || v.block_x > 256 || v.block_x % 32 || v.block_y != 1)
+            return STENCIL_ERR_BADARG;
+        if (fused2d_smem_bytes(v.tile_x, v.tile_y, p.radius, v.fuse) > 227 * 1024)
+            return STENCIL_ERR_UNSUPPORTED;
+        return STENCIL_OK;
+    }
+    return STENCIL_ERR_BADARG;
+}
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ERR_CUDA; }
+
+static int map_launch_rc(int rc) {
+    if (rc == 0) return STENCIL_OK;
+    if (rc == -1) return STENCIL_ERR_BADARG;
+    if (rc == -2) return STENCIL_ERR_UNSUPPORTED;
+    return STENCIL_ERR_CUDA;
+}
+
+size_t dtype_size(int dtype) { return dtype == STENCIL_F32 ? 4 : 2; }
+
+int ensure_scratch(stencil_plan_s &p) {
+    const size_t bytes = (size_t)p.dims[0] * p.dims[1] * p.dims[2] * dtype_size(p.dtype);
+    if (p.scratch && p.scratch_bytes >= bytes) return STENCIL_OK;
+    if (p.scratch) cudaFree(p.scratch);
+    p.scratch = nullptr;
+    p.scratch_bytes = 0;
+    if (cudaMalloc(&p.scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return STENCIL_ERR_OOM;
+    }
+    p.scratch_bytes = bytes;
+    return STENCIL_OK;
+}
+
+// One launch of `k` steps from src to dst with the plan's variant and coefficients.
+static int launch_group(stencil_plan_s &p, const float *cf, const void *src, void *dst, int k,
+                        cudaStream_t s) {
+    const stencil_variant &v = p.variant;
+    if (v.family == STENCIL_FAMILY_FUSED2D) {
+        Fused2DLaunch L;
+        L.ny = p.dims[1];
+        L.nx = p.dims[2];
+        L.shape = p.shape;
+        L.radius = p.radius;
+        L.dtype = p.dtype;
+        L.periodic = p.boundary == STENCIL_PERIODIC;
+        L.coeffs = cf;
+        L.in = src;
+        L.out = dst;
+        L.steps = k;
+        L.tile_x = v.tile_x;
+        L.tile_y = v.tile_y;
+        L.block_threads = v.block_x;
+        L.stream = s;
+        return map_launch_rc(launch_fused2d(L));
+    }
+    StreamLaunch L;
+    L.ndim = p.ndim;
+    L.nz = p.dims[0];
+    L.ny = p.dims[1];
+    L.nx = p.dims[2];
+    L.shape = p.shape;
+    L.radius = p.radius;
+    L.dtype = p.dtype;
+    L.periodic = p.boundary == STENCIL_PERIODIC;
+    L.coeffs = cf;
+    L.in = src;
+    L.out = dst;
+    L.block_x = v.block_x;
+    L.block_y = v.block_y;
+    L.vec_y = v.vec_y;
+    L.z_chunk = v.z_chunk;
+    L.err = nullptr;
+    L.stream = s;
+    return map_launch_rc(launch_stream(L));
+}
+
+// `steps` sweeps in groups of variant.fuse; the groups alternate between `out` and the scratch
+// grid so that the last one writes `out` and `in` is never written.
+int run_steps(stencil_plan_s &p, const float *cf, const void *in, void *out, int steps,
+              cudaStream_t s) {
+    const int fuse = p.variant.family == STENCIL_FAMILY_FUSED2D ? std::max(1, p.variant.fuse) : 1;
+    const int groups = (steps + fuse - 1) / fuse;
+    if (groups > 1) {
+        int rc = ensure_scratch(p);
+        if (rc) return rc;
+    }
+    const void *src = in;
+    int done = 0;
+    for (int g = 0; g < groups; ++g) {
+        const int k = std::min(fuse, steps - done);
+        void *dst = ((groups - 1 - g) % 2 == 0) ? out : p.scratch;
+        int rc = launch_group(p, cf, src, dst, k, s);
+        if (rc) return rc;
+        src = dst;
+        done += k;
+    }
+    return STENCIL_OK;
+}
+
+static bool overlaps(const void *a, const void *b, size_t n) {
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + n && y < x + n;
+}
+
+int check_apply_args(const stencil_plan_s *p, const void *in, const void *out, int steps) {
+    if (!p || !in || !out || steps < 1) return STENCIL_ERR_BADARG;
+    const size_t bytes = (size_t)p->dims[0] * p->dims[1] * p->dims[2] * dtype_size(p->dtype);
+    if (overlaps(in, out, bytes)) return STENCIL_ERR_BADARG;
+    return STENCIL_OK;
+}
+
+}  // namespace gst
+
+using namespace gst;
+
+// =========================================================================================
+// C ABI
+// =========================================================================================
+extern "C" {
+
+int stencil_abi_version(void) { return STENCIL_ABI_VERSION; }
+
+uint64_t stencil_launch_count(void) { return g_launches.load(); }
+
+int stencil_size_class(int64_t cells) { return size_class_of(cells); }
+
+const char *stencil_strerror(int code) {
+    switch (code) {
+    case STENCIL_OK: return "ok";
+    case STENCIL_ERR_BADARG: return "invalid argument";
+    case STENCIL_ERR_UNSUPPORTED: return "unsupported stencil configuration";
+    case STENCIL_ERR_OOM: return "out of memory";
+    case STENCIL_ERR_CUDA: return "CUDA runtime error";
+    case STENCIL_ERR_TIMEOUT: return "device-side wait timed out";
+    case STENCIL_ERR_BOUNDS: return "device-side index check failed";
+    default: return "unknown status code";
+    }
+}
+
+int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, int radius,
+                 int kind, const double *coeffs, int64_t ncoeffs, int dtype, int boundary) {
+    if (!out) return STENCIL_ERR_BADARG;
+    *out = nullptr;
+    if ((ndim != 2 && ndim != 3) || !dims) return STENCIL_ERR_BADARG;
+    if (shape < STENCIL_STAR || shape > STENCIL_DIAMOND) return STENCIL_ERR_BADARG;
+    if (radius < 1 || radius > 4) return STENCIL_ERR_BADARG;
+    if (dtype < STENCIL_F32 || dtype > STENCIL_BF16) return STENCIL_ERR_BADARG;
+    if (boundary != STENCIL_DIRICHLET0 && boundary != STENCIL_PERIODIC) return STENCIL_ERR_BADARG;
+    if (kind < STENCIL_CONST || kind > STENCIL_DIVKGRAD) return STENCIL_ERR_BADARG;
+    int64_t d[3] = {1, 1, 1};
+    for (int i = 0; i < ndim; ++i) {
+        if (dims[i] < 1) return STENCIL_ERR_BADARG;
+        d[3 - ndim + i] = dims[i];
+    }
+    // kernels index one plane with 32-bit integers
+    if (d[1] * d[2] > ((int64_t)1 << 30) || d[0] > ((int64_t)1 << 30)) return STENCIL_ERR_UNSUPPORTED;
+    std::vector<int32_t> offs = make_offsets(ndim, shape, radius);
+    const int64_t npts = (int64_t)offs.size() / ndim;
+    if (kind == STENCIL_CONST) {
+        if (!coeffs || ncoeffs != npts) return STENCIL_ERR_BADARG;
+        for (int64_t i = 0; i < npts; ++i)
+            if (!std::isfinite(coeffs[i])) return STENCIL_ERR_BADARG;
+    } else {
+        if (coeffs || ncoeffs != 0) return STENCIL_ERR_BADARG;
+        if (kind == STENCIL_DIVKGRAD && (shape != STENCIL_STAR || radius != 1))
+            return STENCIL_ERR_BADARG;
+    }
+    stencil_plan_s *p = new (std::nothrow) stencil_plan_s();
+    if (!p) return STENCIL_ERR_OOM;
+    p->ndim = ndim;
+    p->dims[0] = d[0];
+    p->dims[1] = d[1];
+    p->dims[2] = d[2];
+    p->shape = shape;
+    p->radius = radius;
+    p->kind = kind;
+    p->dtype = dtype;
+    p->boundary = boundary;
+    p->npts = npts;
+    p->offsets = offs;
+    if (kind == STENCIL_CONST) {
+        p->coeffs.assign(coeffs, coeffs + npts);
+        p->cf.resize(npts);
+        p->cf_flip.resize(npts);
+        for (int64_t i = 0; i < npts; ++i) p->cf[i] = (float)coeffs[i];
+        // flipped stencil: the coefficient of offset o moves to offset -o
+        for (int64_t i = 0; i < npts; ++i) {
+            for (int64_t j = 0; j < npts; ++j) {
+                bool neg = true;
+                for (int a = 0; a < ndim; ++a)
+                    if (offs[j * ndim + a] != -offs[i * ndim + a]) neg = false;
+                if (neg) p->cf_flip[i] = (float)coeffs[j];
+            }
+        }
+    }
+    stencil_variant v;
+    if (!lookup_map(*p, &v) || validate_variant(*p, v) != STENCIL_OK) v = default_variant(*p);
+    p->variant = v;
+    *out = p;
+    return STENCIL_OK;
+}
+
+int stencil_offsets(stencil_handle h, int32_t *offsets_out, int64_t capacity, int64_t *n) {
+    if (!h || !n || capacity < 0 || (capacity > 0 && !offsets_out)) return STENCIL_ERR_BADARG;
+    *n = h->npts;
+    const int64_t m = std::min(capacity, h->npts);
+    if (m > 0) std::memcpy(offsets_out, h->offsets.data(), sizeof(int32_t) * m * h->ndim);
+    return STENCIL_OK;
+}
+
+int stencil_destroy(stencil_handle h) {
+    if (!h) return STENCIL_OK;
+    if (h->scratch || h->stage_in || h->stage_out || h->d_err) cudaDeviceSynchronize();
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->stage_in) cudaFree(h->stage_in);
+    if (h->stage_out) cudaFree(h->stage_out);
+    if (h->d_err) cudaFree(h->d_err);
+    delete h;
+    return STENCIL_OK;
+}
+
+int stencil_apply(stencil_handle h, const void *in, void *out, int steps, void *stream) {
+    int rc = check_apply_args(h, in, out, steps);
+    if (rc) return rc;
+    if (h->kind != STENCIL_CONST) return STENCIL_ERR_BADARG;
+    return run_steps(*h, h->cf.data(), in, out, steps, (cudaStream_t)stream);
+}
+
+int stencil_apply_adjoint(stencil_handle h, const void *in, void *out, int steps, void *stream) {
+    int rc = check_apply_args(h, in, out, steps);
+    if (rc) return rc;
+    if (h->kind != STENCIL_CONST) return STENCIL_ERR_BADARG;
+    return run_steps(*h, h->cf_flip.data(), in, out, steps, (cudaStream_t)stream);
+}
+
+int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, int steps,
+                       void *stream) {
+    if (!h || !in_host || !out_host || steps < 1) return STENCIL_ERR_BADARG;
+    if (h->kind != STENCIL_CONST) return STENCIL_ERR_BADARG;
+    const size_t bytes = (size_t)h->dims[0] * h->dims[1] * h->dims[2] * dtype_size(h->dtype);
+    if (!h->stage_in || h->stage_bytes < bytes) {
+        if (h->stage_in) cudaFree(h->stage_in);
+        if (h->stage_out) cudaFree(h->stage_out);
+        h->stage_in = h->stage_out = nullptr;
+        h->stage_bytes = 0;
+        if (cudaMalloc(&h->stage_in, bytes) != cudaSuccess ||
+            cudaMalloc(&h->stage_out, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return STENCIL_ERR_OOM;
+        }
+        h->stage_bytes = bytes;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(h->stage_in, in_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return STENCIL_ERR_CUDA;
+    int rc = run_steps(*h, h->cf.data(), h->stage_in, h->stage_out, steps, s);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(out_host, h->stage_out, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return STENCIL_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+int stencil_sync_status(stencil_handle h, void *stream) {
+    if (!h) return STENCIL_ERR_BADARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return STENCIL_ERR_CUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return STENCIL_ERR_CUDA;
+    if (h->d_err) {
+        int v = 0;
+        if (cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return STENCIL_ERR_CUDA;
+        if (v) {
+            cudaMemset(h->d_err, 0, sizeof(int));
+            return v;
+        }
+    }
+    return STENCIL_OK;
+}
+
+int stencil_plan_get_variant(stencil_handle h, stencil_variant *v) {
+    if (!h || !v) return STENCIL_ERR_BADARG;
+    *v = h->variant;
+    return STENCIL_OK;
+}
+
+int stencil_plan_set_variant(stencil_handle h, const stencil_variant *v) {
+    if (!h || !v) return STENCIL_ERR_BADARG;
+    int rc = validate_variant(*h, *v);
+    if (rc) return rc;
+    h->variant = *v;
+    return STENCIL_OK;
+}
+
+int stencil_load_dispatch_map(const char *path) {
+    std::vector<MapEntry> entries;
+    if (path) {
+        FILE *f = std::fopen(path, "r");
+        if (!f) return STENCIL_ERR_BADARG;
+        char line[512];
+        while (std::fgets(line, sizeof(line), f)) {
+            char *hash = std::strchr(line, '#');
+            if (hash) *hash = 0;
+            MapEntry e;
+            std::memset(&e, 0, sizeof(e));
+            int n = std::sscanf(line, "%d %d %d %d %d %d %d : %d %d %d %d %d %d %d %d", &e.key[0],
+                                &e.key[1], &e.key[2], &e.key[3], &e.key[4], &e.key[5], &e.key[6],
+                                &e.v.family, &e.v.block_x, &e.v.block_y, &e.v.vec_y,
+                                &e.v.z_chunk, &e.v.fuse, &e.v.tile_x, &e.v.tile_y);
+            if (n == 15) {
+                entries.push_back(e);
+            } else {
+                bool blank = true;
+                for (char *c = line; *c; ++c)
+                    if (!std::isspace((unsigned char)*c)) blank = false;
+                if (!blank) {
+                    std::fclose(f);
+                    return STENCIL_ERR_BADARG;
+                }
+            }
+        }
+        std::fclose(f);
+    }
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    g_map.swap(entries);
+    return STENCIL_OK;
+}
+
+}  // extern "C"
+
+namespace gst {
+
+int launch_stream(const StreamLaunch &L) {
+#define GST_CASE(DT, ND)                                                  \
+    if (L.ndim == ND) {                                                   \
+        if (L.shape == STENCIL_STAR) return launch_stream_##DT##_##ND##d_star(L);       \
+        if (L.shape == STENCIL_BOX) return launch_stream_##DT##_##ND##d_box(L);         \
+        if (L.shape == STENCIL_DIAMOND) return launch_stream_##DT##_##ND##d_diamond(L); \
+    }
+    switch (L.dtype) {
+    case STENCIL_F32:
+        GST_CASE(f32, 2) GST_CASE(f32, 3) break;
+    case STENCIL_F16:
+        GST_CASE(f16, 2) GST_CASE(f16, 3) break;
+    case STENCIL_BF16:
+        GST_CASE(bf16, 2) GST_CASE(bf16, 3) break;
+    default: break;
+    }
+#undef GST_CASE
+    return -2;
+}
+
+}  // namespace gst

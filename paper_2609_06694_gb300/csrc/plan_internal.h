@@ -1,0 +1,37 @@
+// Plan and batch objects behind the opaque handles of include/stencil.h (host only).
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/stencil.h"
+
+struct stencil_plan_s {
+    int ndim = 0;
+    int64_t dims[3] = {1, 1, 1};  // (nz, ny, nx); nz = 1 for 2D grids
+    int shape = 0, radius = 0, kind = 0, dtype = 0, boundary = 0;
+    int64_t npts = 0;
+    std::vector<int32_t> offsets;  // npts * ndim, canonical order
+    std::vector<double> coeffs;    // STENCIL_CONST: as given
+    std::vector<float> cf;         // f32 coefficients for the kernels
+    std::vector<float> cf_flip;    // coefficient of -o at index of o (adjoint)
+    stencil_variant variant{};
+    void *scratch = nullptr;       // one grid of the storage type (multi-step ping-pong)
+    size_t scratch_bytes = 0;
+    void *stage_in = nullptr;      // staging for stencil_apply_host
+    void *stage_out = nullptr;
+    size_t stage_bytes = 0;
+    int *d_err = nullptr;          // device error word (allocated by the kernels that need one)
+};
+
+namespace gst {
+std::vector<int32_t> make_offsets(int ndim, int shape, int r);
+int size_class_of(int64_t cells);
+int validate_variant(const stencil_plan_s &p, const stencil_variant &v);
+size_t dtype_size(int dtype);
+int ensure_scratch(stencil_plan_s &p);
+int run_steps(stencil_plan_s &p, const float *cf, const void *in, void *out, int steps,
+              cudaStream_t s);
+int check_apply_args(const stencil_plan_s *p, const void *in, const void *out, int steps);
+}  // namespace gst

@@ -1,0 +1,8 @@
+// Streaming-sweep kernels: float storage, 2D grids, diamond offset sets (instantiations only).
+#include "stream_launch.cuh"
+
+namespace gst {
+int launch_stream_f32_2d_diamond(const StreamLaunch &L) {
+    return launch_stream_r<float, 2, kDiamond>(L);
+}
+}  // namespace gst

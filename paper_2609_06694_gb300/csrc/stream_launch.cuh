@@ -1,0 +1,98 @@
+// Host-side launchers of the streaming sweep kernel, instantiated per storage type.
+#pragma once
+
+#include <cstring>
+
+#include "internal.h"
+#include "stream.cuh"
+
+namespace gst {
+
+// The z loop is unrolled by 2R+1 (queue indices become constants) only while the unrolled
+// body stays small; larger stencils rotate their partial-sum queue instead.
+constexpr bool stream_unroll_z(int ndim, int shape, int r, int vx, int vy) {
+    return ndim == 2 || shape_count(ndim, shape, r) * vx * vy * (2 * r + 1) <= 2000;
+}
+
+template <typename T, int NDIM, int SHAPE, int R, int VY>
+int launch_stream_t(const StreamLaunch &L) {
+    constexpr int VX = 16 / (int)sizeof(T);  // one 16-byte vector of cells per thread row
+    constexpr int NSTAGE = 3;
+    constexpr int NPTS = OffsetTable<NDIM, SHAPE, R>::count;
+    constexpr int P = NDIM == 3 ? 2 * R + 1 : 1;
+    constexpr bool UNROLLZ = stream_unroll_z(NDIM, SHAPE, R, VX, VY);
+    using K = StreamKernel<T, NDIM, SHAPE, R, VX, VY, NSTAGE, UNROLLZ>;
+    auto kern = stream_sweep_kernel<T, NDIM, SHAPE, R, VX, VY, NSTAGE, UNROLLZ>;
+
+    const int bx = L.block_x, by = L.block_y;
+    if (bx < 1 || by < 1 || bx * by > 256 || bx * by % 32 != 0) return -1;
+    const int TX = bx * VX, TY = by * VY;
+    const int64_t nx = L.nx, ny = L.ny, nz = NDIM == 3 ? L.nz : 1;
+    if (nx * ny > (int64_t)INT32_MAX - 4 * TX) return -2;
+
+    StreamParams<T> p;
+    p.in = static_cast<const T *>(L.in);
+    p.out = static_cast<T *>(L.out);
+    p.nx = (int)nx;
+    p.ny = (int)ny;
+    p.nz = (int)nz;
+    p.periodic = L.periodic;
+    p.tiles_x = (int)((nx + TX - 1) / TX);
+    p.tiles_y = (int)((ny + TY - 1) / TY);
+    const int zc = (NDIM == 3 && L.z_chunk > 0) ? L.z_chunk : (int)nz;
+    p.zchunk = zc;
+    const int64_t zchunks = NDIM == 3 ? (nz + zc - 1) / zc : 1;
+    const int pitch = TX + 2 * K::A;
+    const int rows = TY + 2 * R;
+    const int nchunks = (pitch / K::A) * rows;
+    p.kchunks = (nchunks + bx * by - 1) / (bx * by);
+    const bool ptr_ok = ((uintptr_t)L.in % 16 == 0) && ((uintptr_t)L.out % 16 == 0);
+    p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0 && p.kchunks <= K::KMAX) ? 1 : 0;
+    p.err = L.err;
+
+    ConstCoeffs<NPTS> cf;
+    for (int i = 0; i < NPTS; ++i) cf.c[i] = L.coeffs[i];
+
+    const int64_t nblocks = (int64_t)p.tiles_x * p.tiles_y * zchunks;
+    if (nblocks > INT32_MAX) return -2;
+    const size_t smem = K::smem_bytes(bx, by);
+    static size_t smem_set = 0;  // per instantiation
+    if (smem > 48 * 1024 && smem > smem_set) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -4;
+        smem_set = smem;
+    }
+    kern<<<(unsigned)nblocks, dim3(bx, by), smem, L.stream>>>(p, cf);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <typename T, int NDIM, int SHAPE, int R> int launch_stream_vy(const StreamLaunch &L) {
+    if (L.vec_y == 1) return launch_stream_t<T, NDIM, SHAPE, R, 1>(L);
+    if constexpr (stream_vy_compiled(NDIM, SHAPE, R, 2)) {
+        if (L.vec_y == 2) return launch_stream_t<T, NDIM, SHAPE, R, 2>(L);
+    }
+    return -2;
+}
+
+template <typename T, int NDIM, int SHAPE> int launch_stream_r(const StreamLaunch &L) {
+    switch (L.radius) {
+    case 1: return launch_stream_vy<T, NDIM, SHAPE, 1>(L);
+    case 2: return launch_stream_vy<T, NDIM, SHAPE, 2>(L);
+    case 3: return launch_stream_vy<T, NDIM, SHAPE, 3>(L);
+    case 4: return launch_stream_vy<T, NDIM, SHAPE, 4>(L);
+    default: return -2;
+    }
+}
+
+template <typename T, int NDIM> int launch_stream_shape(const StreamLaunch &L) {
+    switch (L.shape) {
+    case kStar: return launch_stream_r<T, NDIM, kStar>(L);
+    case kBox: return launch_stream_r<T, NDIM, kBox>(L);
+    case kDiamond: return launch_stream_r<T, NDIM, kDiamond>(L);
+    default: return -2;
+    }
+}
+
+}  // namespace gst

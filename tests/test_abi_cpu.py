@@ -1,0 +1,185 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every function
+declared in include/*.h, validates plans and arguments, keeps the canonical offset order, and
+reads dispatch maps."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2609_06694_gb300 as gs
+from paper_2609_06694_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_core_entry_points():
+    names = declared_functions()
+    for n in ("stencil_plan", "stencil_apply", "stencil_apply_adjoint", "stencil_apply_var",
+              "stencil_apply_adjoint_var", "stencil_batch_plan", "stencil_batch_launch",
+              "stencil_destroy", "stencil_strerror", "stencil_sync_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function():
+    lib = ctypes.CDLL(build.LIB)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_abi_version_and_strerror():
+    assert gs.stencil_abi_version() == 1
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        s = gs.stencil_strerror(code)
+        assert s and s != "unknown status code"
+    assert gs.stencil_strerror(-99) == "unknown status code"
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("shape", ["star", "box", "diamond"])
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+def test_library_offsets_equal_oracle_offsets(ndim, shape, r):
+    offs = oracle.offsets(ndim, shape, r)
+    dims = (9, 10, 11)[:ndim]
+    p = gs.stencil_plan(ndim, dims, shape, r, "const", np.ones(len(offs)), "f32", "periodic")
+    assert np.array_equal(gs.stencil_offsets(p), offs)
+
+
+def _plan_rc(ndim=3, dims=(8, 8, 8), shape=0, r=1, kind=0, coeffs="auto", dtype=0, bc=0):
+    lib = api._lib()
+    d = (ctypes.c_int64 * max(1, len(dims)))(*dims)
+    if isinstance(coeffs, str):
+        n = len(oracle.offsets(ndim, ["star", "box", "diamond"][shape], r)) if 1 <= r <= 4 and \
+            ndim in (2, 3) and shape in (0, 1, 2) else 1
+        coeffs = np.ones(n)
+    if coeffs is None:
+        cptr, n = None, 0
+    else:
+        coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+        cptr, n = coeffs.ctypes.data_as(ctypes.c_void_p), len(coeffs)
+    h = ctypes.c_void_p()
+    rc = lib.stencil_plan(ctypes.byref(h), ndim, d, shape, r, kind, cptr, n, dtype, bc)
+    if h.value:
+        lib.stencil_destroy(h)
+    return rc
+
+
+def test_plan_validation():
+    assert _plan_rc() == 0
+    assert _plan_rc(ndim=1, dims=(8,)) == -1
+    assert _plan_rc(ndim=4, dims=(8, 8, 8, 8)) == -1
+    assert _plan_rc(r=0) == -1
+    assert _plan_rc(r=5) == -1
+    assert _plan_rc(shape=3) == -1
+    assert _plan_rc(dtype=3) == -1
+    assert _plan_rc(bc=2) == -1
+    assert _plan_rc(kind=3) == -1
+    assert _plan_rc(dims=(8, 0, 8)) == -1
+    assert _plan_rc(dims=(8, -3, 8)) == -1
+    assert _plan_rc(coeffs=np.ones(6)) == -1          # 7 offsets expected
+    assert _plan_rc(coeffs=None) == -1                # const needs coefficients
+    bad = np.ones(7)
+    bad[3] = np.nan
+    assert _plan_rc(coeffs=bad) == -1
+    assert _plan_rc(kind=1, coeffs=None) == 0         # var: arrays come at apply time
+    assert _plan_rc(kind=1, coeffs=np.ones(7)) == -1
+    assert _plan_rc(kind=2, coeffs=None) == 0         # div(k grad u): star r1 only
+    assert _plan_rc(kind=2, shape=1, coeffs=None) == -1
+    assert _plan_rc(kind=2, r=2, coeffs=None) == -1
+    assert _plan_rc(ndim=2, dims=(5, 7)) == 0
+    assert _plan_rc(dims=(1, 1, 1)) == 0
+    lib = api._lib()
+    assert lib.stencil_plan(None, 3, (ctypes.c_int64 * 3)(8, 8, 8), 0, 1, 0, None, 0, 0, 0) == -1
+
+
+def test_apply_argument_validation_needs_no_device():
+    p = gs.stencil_plan(3, (8, 8, 8), "star", 1, "const", np.ones(7), "f32", "dirichlet")
+    lib = api._lib()
+    buf = ctypes.c_void_p(0x10000000)
+    other = ctypes.c_void_p(0x20000000)
+    assert lib.stencil_apply(None, buf, other, 1, None) == -1
+    assert lib.stencil_apply(p.handle, None, other, 1, None) == -1
+    assert lib.stencil_apply(p.handle, buf, None, 1, None) == -1
+    assert lib.stencil_apply(p.handle, buf, other, 0, None) == -1
+    assert lib.stencil_apply(p.handle, buf, buf, 1, None) == -1        # in == out
+    assert lib.stencil_apply(p.handle, buf, ctypes.c_void_p(0x10000000 + 8), 1, None) == -1
+    assert lib.stencil_apply_adjoint(p.handle, buf, buf, 1, None) == -1
+    assert lib.stencil_apply_host(p.handle, None, other, 1, None) == -1
+    pv = gs.stencil_plan(3, (8, 8, 8), "star", 1, "var", None, "f32", "dirichlet")
+    assert lib.stencil_apply(pv.handle, buf, other, 1, None) == -1    # wrong entry for kind
+
+
+def test_variant_get_set_and_validation():
+    p = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "periodic")
+    v = gs.stencil_plan_get_variant(p)
+    assert v["family"] == gs.FAMILY_STREAM and v["fuse"] == 1
+    gs.stencil_plan_set_variant(p, block_x=32, block_y=4, vec_y=2, z_chunk=16)
+    assert gs.stencil_plan_get_variant(p)["z_chunk"] == 16
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(p, block_x=32, block_y=16)   # 512 threads
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(p, family=gs.FAMILY_FUSED2D, fuse=2, tile_x=32, tile_y=32,
+                                    block_x=128, block_y=1)     # fused 2D on a 3D plan
+    assert gs.stencil_plan_get_variant(p)["z_chunk"] == 16      # unchanged on failure
+    q = gs.stencil_plan(3, (64, 64, 64), "box", 4, "const", np.ones(729), "f32", "periodic")
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(q, vec_y=2)                  # not compiled for box r4
+    p2 = gs.stencil_plan(2, (512, 512), "star", 1, "const", np.full(5, 0.2), "f32", "dirichlet")
+    v2 = gs.stencil_plan_get_variant(p2)
+    assert v2["family"] == gs.FAMILY_FUSED2D and v2["fuse"] > 1
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(p2, tile_x=512, tile_y=512)  # shared memory too large
+
+
+def test_dispatch_map_file(tmp_path):
+    m = tmp_path / "map.txt"
+    m.write_text("# ndim shape r dtype bc kind class : family bx by vy zc fuse tx ty\n"
+                 "3 0 4 0 1 0 -1 : 1 32 8 1 48 1 0 0\n\n")
+    gs.stencil_load_dispatch_map(str(m))
+    try:
+        p = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "periodic")
+        v = gs.stencil_plan_get_variant(p)
+        assert (v["block_x"], v["block_y"], v["vec_y"], v["z_chunk"]) == (32, 8, 1, 48)
+        q = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "dirichlet")
+        assert gs.stencil_plan_get_variant(q)["z_chunk"] != 48   # key differs (boundary)
+        bad = tmp_path / "bad.txt"
+        bad.write_text("3 0 4 : nonsense\n")
+        with pytest.raises(gs.StencilError):
+            gs.stencil_load_dispatch_map(str(bad))
+        with pytest.raises(gs.StencilError):
+            gs.stencil_load_dispatch_map(str(tmp_path / "missing.txt"))
+    finally:
+        gs.stencil_load_dispatch_map(None)
+    p = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "periodic")
+    assert gs.stencil_plan_get_variant(p)["z_chunk"] != 48
+
+
+def test_size_classes():
+    assert [gs.stencil_size_class(n) for n in (1, 1 << 16, 1 << 20, 1 << 24, 1 << 30)] == \
+        [0, 1, 2, 3, 3]
+
+
+def test_library_missing_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(api, "_LIB", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        api._lib()

@@ -1,0 +1,240 @@
+"""GPU parity of the constant-coefficient sweeps against the FP64 oracle (through the C ABI).
+
+Cases span every shape (star, box, diamond), radius 1-4, 2D and 3D grids, f32/f16/bf16
+storage and both boundary rules, on grids that cover several tiles plus ragged tails in x, y
+and z, on the vectorised (16-byte aligned rows) and scalar (odd row length) loaders, and the
+fused multi-step 2D kernel.  Tolerances: max-norm relative error 1e-5 (f32), 2e-3 (f16),
+1e-2 (bf16).  Multi-step low-precision runs are held to the same tolerance against the
+oracle that rounds to the storage type after every step (the library's stated semantics) and
+their error against pure FP64 is reported.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2609_06694_gb300 as gs
+from helpers import TOL, cone_reference, make_input, oracle_run, relerr, seeded_weights
+from paper_2609_06694_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = ["star", "box", "diamond"]
+DTYPES = ["f32", "f16", "bf16"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dev():
+    gs.build.build()
+    torch.cuda.set_device(0)
+
+
+def gpu_apply(plan, x_cpu, steps=1, adjoint=False):
+    xd = x_cpu.cuda()
+    yd = torch.empty_like(xd)
+    fn = gs.stencil_apply_adjoint if adjoint else gs.stencil_apply
+    fn(plan, xd, yd, steps)
+    assert gs.stencil_sync_status(plan) == 0
+    return inputs.stored_values(yd)
+
+
+def dims_for(ndim, shape, r, aligned=True):
+    # x spans 2+ tiles of 128 cells plus a tail; y spans 2+ tiles; z several chunks
+    nx = 264 if aligned else 263
+    if ndim == 2:
+        return (53, nx)
+    big = shape != "star" and r >= 3
+    return (13 if big else 21, 35, nx if not big else (136 if aligned else 133))
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_single_sweep_matches_oracle(ndim, shape, r, dtype, bc):
+    dims = dims_for(ndim, shape, r)
+    offs = oracle.offsets(ndim, shape, r)
+    c = seeded_weights(1000 + r, len(offs))
+    plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, dtype, bc)
+    if ndim == 3:
+        gs.stencil_plan_set_variant(plan, z_chunk=8)  # several z chunks with a ragged tail
+    x, x64 = make_input(2000 + r, dims, dtype)
+    got = gpu_apply(plan, x)
+    ref = oracle.sweep_const(x64, offs, c, bc)
+    assert relerr(got, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_scalar_loader_odd_row_length(ndim, shape, bc):
+    r = 2
+    dims = dims_for(ndim, shape, r, aligned=False)
+    offs = oracle.offsets(ndim, shape, r)
+    c = seeded_weights(31, len(offs))
+    for dtype in DTYPES:
+        plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, dtype, bc)
+        if ndim == 2:
+            gs.stencil_plan_set_variant(plan, family=gs.FAMILY_STREAM, block_x=128 // (
+                4 if dtype == "f32" else 8), block_y=4, vec_y=2, fuse=1, tile_x=0, tile_y=0)
+        x, x64 = make_input(32, dims, dtype)
+        assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, bc)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("vec_y", [1, 2])
+@pytest.mark.parametrize("blocks", [(32, 8), (32, 4), (16, 8), (64, 2)])
+def test_stream_variants_agree(shape, vec_y, blocks):
+    r = 1
+    dims = (19, 45, 200)
+    offs = oracle.offsets(3, shape, r)
+    c = seeded_weights(41, len(offs))
+    plan = gs.stencil_plan(3, dims, shape, r, "const", c, "f32", "periodic")
+    gs.stencil_plan_set_variant(plan, block_x=blocks[0], block_y=blocks[1], vec_y=vec_y,
+                                z_chunk=7)
+    x, x64 = make_input(42, dims, "f32")
+    assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, "periodic")) < 1e-5
+
+
+def test_tiny_grids_wrap_many_times():
+    for ndim, dims in ((3, (3, 2, 4)), (3, (1, 1, 8)), (2, (1, 4)), (2, (3, 5)), (3, (2, 3, 5))):
+        for shape in SHAPES:
+            r = 4
+            offs = oracle.offsets(ndim, shape, r)
+            c = seeded_weights(51, len(offs))
+            for bc in ("periodic", "dirichlet"):
+                plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, "f32", bc)
+                x, x64 = make_input(52, dims, "f32")
+                got = gpu_apply(plan, x)
+                assert relerr(got, oracle.sweep_const(x64, offs, c, bc)) < 1e-5, (dims, shape, bc)
+
+
+@pytest.mark.parametrize("ndim,shape,r", [(3, "star", 4), (3, "box", 1), (3, "diamond", 2),
+                                          (2, "box", 2), (2, "star", 3)])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_multi_step_matches_oracle(ndim, shape, r, dtype, bc):
+    dims = (17, 33, 136) if ndim == 3 else (67, 136)
+    steps = 5
+    offs = oracle.offsets(ndim, shape, r)
+    c = seeded_weights(61, len(offs))
+    plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, dtype, bc)
+    x, x64 = make_input(62, dims, dtype)
+    got = gpu_apply(plan, x, steps)
+    pure, emu = oracle_run(x64, offs, c, bc, steps, dtype)
+    assert relerr(got, emu) < TOL[dtype]
+    assert relerr(got, pure) < 4 * TOL[dtype]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("r", [1, 2, 4])
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_fused2d_matches_oracle(shape, r, dtype, bc):
+    dims = (75, 93)  # ragged against 32x32 tiles
+    offs = oracle.offsets(2, shape, r)
+    c = seeded_weights(71, len(offs))
+    plan = gs.stencil_plan(2, dims, shape, r, "const", c, dtype, bc)
+    gs.stencil_plan_set_variant(plan, family=gs.FAMILY_FUSED2D, fuse=3, tile_x=32, tile_y=32,
+                                block_x=128, block_y=1, vec_y=1, z_chunk=0)
+    x, x64 = make_input(72, dims, dtype)
+    steps = 7  # fused groups of 3, 3, 1
+    got = gpu_apply(plan, x, steps)
+    pure, emu = oracle_run(x64, offs, c, bc, steps, dtype)
+    assert relerr(got, emu) < TOL[dtype]
+
+
+def test_fused_equals_unfused_bitwise():
+    """Rounding between fused steps makes grouping irrelevant (same FP32 sums per step)."""
+    dims = (70, 90)
+    offs = oracle.offsets(2, "box", 1)
+    c = seeded_weights(81, len(offs))
+    for dtype in DTYPES:
+        x, _ = make_input(82, dims, dtype)
+        a = gs.stencil_plan(2, dims, "box", 1, "const", c, dtype, "dirichlet")
+        gs.stencil_plan_set_variant(a, family=gs.FAMILY_FUSED2D, fuse=6, tile_x=32, tile_y=16,
+                                    block_x=64, block_y=1, vec_y=1, z_chunk=0)
+        b = gs.stencil_plan(2, dims, "box", 1, "const", c, dtype, "dirichlet")
+        gs.stencil_plan_set_variant(b, family=gs.FAMILY_FUSED2D, fuse=1, tile_x=32, tile_y=16,
+                                    block_x=64, block_y=1, vec_y=1, z_chunk=0)
+        ya, yb = gpu_apply(a, x, 6), gpu_apply(b, x, 6)
+        assert np.array_equal(ya, yb)
+
+
+@pytest.mark.parametrize("ndim,shape,r", [(3, "box", 1), (3, "star", 2), (2, "diamond", 3),
+                                          (2, "box", 2)])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_adjoint_matches_oracle_and_dot_test(ndim, shape, r, bc):
+    dims = (15, 22, 136) if ndim == 3 else (41, 136)
+    offs = oracle.offsets(ndim, shape, r)
+    c = inputs.uniform(91, (len(offs),))  # non-symmetric weights
+    plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, "f32", bc)
+    x, x64 = make_input(92, dims, "f32")
+    y, y64 = make_input(93, dims, "f32")
+    aty = gpu_apply(plan, y, 1, adjoint=True)
+    assert relerr(aty, oracle.sweep_const_adjoint(y64, offs, c, bc)) < 1e-5
+    ax = gpu_apply(plan, x, 1)
+    lhs, rhs = float(np.sum(ax * y64)), float(np.sum(x64 * aty))
+    assert abs(lhs - rhs) <= 1e-5 * np.sum(np.abs(ax * y64))
+    aty3 = gpu_apply(plan, y, 3, adjoint=True)
+    ref3 = oracle.run(y64, "const", bc, 3, offs=offs, coeffs=c, adjoint=True)
+    assert relerr(aty3, ref3) < 1e-5
+
+
+def test_jacobi_512_10_steps_full_size():
+    """2D 5-point Jacobi, weights 0.2, zero Dirichlet, 512^2, 10 steps (fused launches)."""
+    dims = (512, 512)
+    offs = oracle.offsets(2, "star", 1)
+    c = np.full(len(offs), 0.2)
+    plan = gs.stencil_plan(2, dims, "star", 1, "const", c, "f32", "dirichlet")
+    assert gs.stencil_plan_get_variant(plan)["family"] == gs.FAMILY_FUSED2D
+    x, x64 = make_input(1001, dims, "f32")
+    got = gpu_apply(plan, x, 10)
+    ref = oracle.run(x64, "const", "dirichlet", 10, offs=offs, coeffs=c)
+    assert relerr(got, ref) < 1e-5
+
+
+def _laplacian_r4_plan(dims, bc="periodic"):
+    offs = oracle.offsets(3, "star", 4)
+    return offs, inputs.laplacian_coeffs(offs, 4)
+
+
+@pytest.mark.parametrize("which", ["star4", "box27"])
+def test_full_size_512_cubed_samples(which):
+    """512^3 f32 periodic, in the launch configuration the benchmark times: 1 step checked at
+    sampled cells against the oracle's point evaluation, 8 steps at sampled cells through the
+    dependency cone."""
+    dims = (512, 512, 512)
+    if which == "star4":
+        shape, r = "star", 4
+        offs = oracle.offsets(3, shape, r)
+        c = inputs.laplacian_coeffs(offs, 4)
+        seed = 2001
+    else:
+        shape, r = "box", 1
+        offs = oracle.offsets(3, shape, r)
+        c, _ = inputs.normalised_sum_weights(2002, len(offs))
+        seed = 2003
+    plan = gs.stencil_plan(3, dims, shape, r, "const", c, "f32", "periodic")
+    x = inputs.to_storage(inputs.uniform(seed, dims), "f32")
+    xd = x.cuda()
+    y1 = torch.empty_like(xd)
+    gs.stencil_apply(plan, xd, y1, 1)
+    y8 = torch.empty_like(xd)
+    gs.stencil_apply(plan, xd, y8, 8)
+    assert gs.stencil_sync_status(plan) == 0
+    x64 = inputs.stored_values(x)
+    rng = np.random.default_rng(5)
+    pts = [tuple(int(v) for v in rng.integers(0, 512, 3)) for _ in range(200)]
+    pts += [(0, 0, 0), (511, 511, 511), (0, 511, 3), (255, 0, 511)]
+    lin = [(p[0] * 512 + p[1]) * 512 + p[2] for p in pts]
+    ref1 = oracle.sweep_const_points(x64, offs, c, "periodic", lin)
+    got1 = y1.flatten()[torch.tensor(lin, device="cuda")].double().cpu().numpy()
+    assert relerr(got1, ref1) < 1e-5
+    scale1 = float(y1.abs().max())
+    assert np.max(np.abs(got1 - ref1)) / scale1 < 1e-5
+    sel = pts[:6]
+    ref8 = np.array([cone_reference(x64, offs, c, "periodic", 8, p) for p in sel])
+    got8 = np.array([float(y8[p]) for p in sel])
+    assert np.max(np.abs(got8 - ref8)) / float(y8.abs().max()) < 1e-5
