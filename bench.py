@@ -107,14 +107,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(device):
+def build_workload(device, n=N):
     """Plans and device-resident inputs/outputs of the four sub-workloads."""
     import torch
 
     import paper_2609_06694_gb300 as gs
     from paper_2609_06694_gb300 import inputs
 
-    dims = (N, N, N)
+    dims = (n, n, n)
     star = gs.stencil_plan(3, dims, "star", 4, "const", np.ones(25), "f32", "periodic")
     offs_s = gs.stencil_offsets(star)
     c_star = inputs.laplacian_coeffs(offs_s, 4)
@@ -129,11 +129,13 @@ def build_workload(device):
             "c_star": c_star, "c_box": c_box, "offs_star": offs_s}
 
 
-def run_step(gs, W, stream, ev=None):
+def run_step(gs, W, stream, ev=None, only=None):
     """The 18 sweeps; with ev, records events around each call: [(name, launches, s, e)]."""
     import torch
     calls = (("star", "x_star", 1), ("star", "x_star", 8), ("box", "x_box", 1),
              ("box", "x_box", 8))
+    if only:
+        calls = ((only, "x_" + only, 1),)
     for name, xin, steps in calls:
         if ev is not None:
             s = torch.cuda.Event(enable_timing=True)
@@ -178,8 +180,18 @@ def bench_ours(args):
     build.build()
     import paper_2609_06694_gb300 as gs
 
-    W = build_workload(device)
+    W = build_workload(device, args.grid)
     stream = torch.cuda.current_stream(device)
+    if args.only:
+        # single-sweep profiling case (not a benchmark line)
+        for _ in range(args.warmup + args.steps):
+            run_step(gs, W, stream, only=args.only)
+        torch.cuda.synchronize()
+        rc = gs.stencil_sync_status(W[args.only])
+        print(json.dumps({"profile_case": args.only, "grid": args.grid, "status": rc}))
+        if rc:
+            raise SystemExit(1)
+        return
     for _ in range(args.warmup):
         run_step(gs, W, stream)
     torch.cuda.synchronize()
@@ -237,7 +249,7 @@ def bench_ours(args):
     xs = W["x_star_host"].pin_memory()
     xb = W["x_box_host"].pin_memory()
     yh = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
 
     def e2e_step():
         gs.stencil_apply_host(W["star"], xs, yh, 1, stream=stream)
@@ -245,20 +257,22 @@ def bench_ours(args):
         gs.stencil_apply_host(W["box"], xb, yh, 1, stream=stream)
         gs.stencil_apply_host(W["box"], xb, yh, 8, stream=stream)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    h0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e_val = None
+    if e2e_steps:
         e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - h0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = SWEEPS_PER_STEP * CELLS * e2e_steps * world / e2e_s / 1e9
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        h0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - h0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_val = round(SWEEPS_PER_STEP * CELLS * e2e_steps * world / e2e_s / 1e9, 3)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -277,7 +291,7 @@ def bench_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": round(e2e_val, 3), "unit": "Gcell-updates/s",
+            "e2e": {"value": e2e_val, "unit": "Gcell-updates/s",
                     "h2d_bytes_per_step": 4 * CELLS * 4, "d2h_bytes_per_step": 4 * CELLS * 4,
                     "api": "stencil_apply_host (pinned host buffers)"},
             "gpu_launches": int(launches),
@@ -352,10 +366,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", choices=["star", "box"], default=None,
+                    help="profiling case: only the 1-sweep call of one stencil, no JSON line")
+    ap.add_argument("--grid", type=int, default=N, help="cube side (profiling cases only)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: at least 3 warm-up steps are required; using 3", file=sys.stderr)
         args.warmup = 3
+    if args.only is None:
+        args.grid = N  # the benchmark line is always the 512^3 workload
     if args.impl == "reference":
         bench_reference(args)
     else:
