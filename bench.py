@@ -184,11 +184,14 @@ def bench_ours(args):
     stream = torch.cuda.current_stream(device)
     if args.only:
         # single-sweep profiling case (not a benchmark line)
+        if args.variant:
+            gs.stencil_plan_set_variant(W[args.only], **json.loads(args.variant))
         for _ in range(args.warmup + args.steps):
             run_step(gs, W, stream, only=args.only)
         torch.cuda.synchronize()
         rc = gs.stencil_sync_status(W[args.only])
-        print(json.dumps({"profile_case": args.only, "grid": args.grid, "status": rc}))
+        print(json.dumps({"profile_case": args.only, "grid": args.grid, "status": rc,
+                          "variant": gs.stencil_plan_get_variant(W[args.only])}))
         if rc:
             raise SystemExit(1)
         return
@@ -370,6 +373,8 @@ def main():
     ap.add_argument("--only", choices=["star", "box"], default=None,
                     help="profiling case: only the 1-sweep call of one stencil, no JSON line")
     ap.add_argument("--grid", type=int, default=N, help="cube side (profiling cases only)")
+    ap.add_argument("--variant", default=None,
+                    help="profiling case: JSON dict of stencil_variant fields to force")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: at least 3 warm-up steps are required; using 3", file=sys.stderr)

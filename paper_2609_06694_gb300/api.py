@@ -186,6 +186,10 @@ def stencil_apply_adjoint(plan: Plan, inp, out, steps=1, stream=None):
 
 
 def _coeff_ptrs(plan: Plan, arrays):
+    # the C entry point reads exactly this many pointers, so the count is checked here
+    want = 1 if plan.kind == "divkgrad" else len(stencil_offsets(plan))
+    if len(arrays) != want:
+        raise ValueError(f"expected {want} coefficient arrays, got {len(arrays)}")
     for i, a in enumerate(arrays):
         plan._check_tensor(a, f"coeff_arrays[{i}]")
     return (ctypes.c_void_p * len(arrays))(*[a.data_ptr() for a in arrays])

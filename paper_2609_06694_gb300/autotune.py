@@ -1,0 +1,185 @@
+"""Autotuner that fills the dispatch map (ForgeStencil Sec. 4.3: the kernel is specialised per
+stencil type, grid shape and precision; here the specialisation is chosen by measurement).
+
+For each tuning key (ndim, shape, radius, dtype, boundary, kind, size class) it times every
+candidate kernel variant on a representative grid with CUDA events (median of several runs,
+inputs larger than L2 for the 3D cases), and records the fastest together with its achieved
+bandwidth (algorithmic bytes / time) and fraction of the measured HBM peak.  The result is a
+text map read by ``stencil_load_dispatch_map`` (one line per key) plus a JSON evidence file.
+
+Usage on a GPU:  python -m paper_2609_06694_gb300.autotune [--out DIR] [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import os
+import time
+
+import numpy as np
+
+from . import api as gs
+from . import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_MAP = os.path.join(HERE, "dispatch_map.txt")
+DEFAULT_EVIDENCE = os.path.join(HERE, "dispatch_evidence.json")
+
+SHAPE_ID = gs.SHAPES
+DTYPE_ID = gs.DTYPES
+BC_ID = gs.BOUNDARIES
+KIND_ID = gs.KINDS
+
+
+def stream_candidates(ndim, shape, radius, dtype, quick=False):
+    es = 4 if dtype == "f32" else 2
+    bx = 128 // (16 // es)
+    out = []
+    vys = [1, 2] if (ndim == 2 or shape == "star" or radius <= 2) else [1]
+    if radius == 1:
+        vys.append(4)
+    bys = [b for b in (1, 2, 4, 8, 16) if 32 <= bx * b <= 256 and (bx * b) % 32 == 0]
+    zcs = [0] if ndim == 2 else ([64, 128] if quick else [32, 64, 128, 256])
+    for vy, by, zc in itertools.product(vys, bys, zcs):
+        out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=vy, z_chunk=zc,
+                        fuse=1, tile_x=0, tile_y=0))
+    return out
+
+
+def fused2d_candidates(radius, steps):
+    out = []
+    for fuse in sorted({1, 2, 4, 5, 8, 10} & set(range(1, steps + 1)) | {steps}):
+        for tile in ((32, 32), (64, 32), (64, 64), (128, 32)):
+            for threads in (128, 256):
+                out.append(dict(family=gs.FAMILY_FUSED2D, block_x=threads, block_y=1, vec_y=1,
+                                z_chunk=0, fuse=fuse, tile_x=tile[0], tile_y=tile[1]))
+    return out
+
+
+def time_variant(plan, xin, y, steps, variant, reps=5, warmup=2):
+    import torch
+    try:
+        gs.stencil_plan_set_variant(plan, **variant)
+    except gs.StencilError:
+        return None
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        gs.stencil_apply(plan, xin, y, steps)
+    ts = []
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        gs.stencil_apply(plan, xin, y, steps)
+        e.record(stream)
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    if gs.stencil_sync_status(plan) != 0:
+        return None
+    return float(np.median(ts))
+
+
+def hbm_peak():
+    path = os.path.join(os.path.dirname(HERE), "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=print):
+    """Time every candidate on `dims`; returns (best_variant, evidence list)."""
+    import torch
+    c = inputs.normalised_abs_weights(7, _npts(ndim, shape, radius))
+    plan = gs.stencil_plan(ndim, dims, shape, radius, "const", c, dtype, bc)
+    x = inputs.to_storage(inputs.uniform(8, dims), dtype).cuda()
+    y = torch.empty_like(x)
+    cands = stream_candidates(ndim, shape, radius, dtype, quick)
+    if ndim == 2 and steps > 1:
+        cands += fused2d_candidates(radius, steps)
+    es = 4 if dtype == "f32" else 2
+    cells = int(np.prod(dims))
+    peak = hbm_peak()
+    ev = []
+    for v in cands:
+        ms = time_variant(plan, x, y, steps, v)
+        if ms is None:
+            continue
+        gbs = 2 * es * cells * steps / (ms * 1e-3) / 1e9
+        ev.append({"variant": v, "ms": round(ms, 5), "alg_GBps": round(gbs, 1),
+                   "frac_hbm": round(gbs / peak, 4)})
+    ev.sort(key=lambda e: e["ms"])
+    if ev:
+        b = ev[0]
+        log(f"  {ndim}D {shape} r{radius} {dtype} {bc} {dims} x{steps}: best {b['ms']:.4f} ms "
+            f"{b['alg_GBps']} GB/s ({b['frac_hbm']:.2%}) {b['variant']}")
+    return (ev[0]["variant"] if ev else None), ev
+
+
+def _npts(ndim, shape, r):
+    if shape == "star":
+        return 2 * ndim * r + 1
+    if shape == "box":
+        return (2 * r + 1) ** ndim
+    if ndim == 2:
+        return 2 * r * r + 2 * r + 1
+    return (2 * r + 1) * (2 * r * r + 2 * r + 3) // 3
+
+
+# Tuning set: (ndim, dims, shape, radius, dtype, boundary, steps)
+def tuning_set(quick=False):
+    s = []
+    big = (512, 512, 512)
+    for shape, r in (("star", 4), ("box", 1)):
+        s.append((3, big, shape, r, "f32", "periodic", 1))
+    if not quick:
+        mid = (384, 384, 384)
+        for shape, r in (("star", 1), ("star", 2), ("box", 2), ("diamond", 2)):
+            s.append((3, mid, shape, r, "f32", "periodic", 1))
+        for dtype in ("f16", "bf16"):
+            s.append((3, mid, "star", 1, dtype, "dirichlet", 1))
+        s.append((2, (512, 512), "star", 1, "f32", "dirichlet", 10))
+        for shape, r in (("star", 1), ("star", 2), ("box", 1), ("box", 2)):
+            s.append((2, (2048, 2048), shape, r, "f32", "dirichlet", 1))
+    return s
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=DEFAULT_MAP)
+    ap.add_argument("--evidence", default=DEFAULT_EVIDENCE)
+    ap.add_argument("--quick", action="store_true")
+    args = ap.parse_args()
+    from . import build
+    build.build()
+    torch.cuda.set_device(0)
+    gs.stencil_load_dispatch_map(None)
+    lines = ["# dispatch map written by paper_2609_06694_gb300.autotune on "
+             + torch.cuda.get_device_name(0),
+             "# ndim shape radius dtype boundary kind size_class : "
+             "family block_x block_y vec_y z_chunk fuse tile_x tile_y"]
+    evidence = []
+    for ndim, dims, shape, r, dtype, bc, steps in tuning_set(args.quick):
+        best, ev = tune_key(ndim, dims, shape, r, dtype, bc, steps, args.quick)
+        if best is None:
+            continue
+        cls = gs.stencil_size_class(int(np.prod(dims)))
+        key = [ndim, SHAPE_ID[shape], r, DTYPE_ID[dtype], BC_ID[bc], KIND_ID["const"], cls]
+        val = [best[k] for k in ("family", "block_x", "block_y", "vec_y", "z_chunk", "fuse",
+                                 "tile_x", "tile_y")]
+        lines.append(" ".join(map(str, key)) + " : " + " ".join(map(str, val)))
+        evidence.append({"key": {"ndim": ndim, "dims": list(dims), "shape": shape, "radius": r,
+                                 "dtype": dtype, "boundary": bc, "steps": steps,
+                                 "size_class": cls}, "candidates": ev})
+    with open(args.out, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    with open(args.evidence, "w") as f:
+        json.dump({"device": torch.cuda.get_device_name(0), "when": time.strftime("%F %T"),
+                   "hbm_peak_GBps": hbm_peak(), "keys": evidence}, f, indent=1)
+    print(f"wrote {args.out} and {args.evidence}")
+
+
+if __name__ == "__main__":
+    main()

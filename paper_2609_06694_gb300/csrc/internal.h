@@ -37,10 +37,11 @@ GST_DECLARE_STREAM(bf16, 3)
 int launch_stream(const StreamLaunch &L);  // dispatches on dtype, ndim and shape
 
 // Rows per thread compiled for a streaming kernel: 1 always; 2 for every 2D stencil, every 3D
-// star and 3D box/diamond up to radius 2 (wider 3D stencils are ALU-heavy enough that the
-// second row's registers cost more than the shared-memory reads they save).
+// star and 3D box/diamond up to radius 2; 4 for radius 1 (wider 3D stencils are ALU-heavy
+// enough that more rows cost more registers than the shared-memory reads they save).
 constexpr bool stream_vy_compiled(int ndim, int shape, int radius, int vec_y) {
-    return vec_y == 1 || (vec_y == 2 && (ndim == 2 || shape == 0 || radius <= 2));
+    return vec_y == 1 || (vec_y == 2 && (ndim == 2 || shape == 0 || radius <= 2)) ||
+           (vec_y == 4 && radius == 1);
 }
 
 // Several 2D time steps in one launch (shared-memory tile with a shrinking halo).
@@ -58,6 +59,29 @@ struct Fused2DLaunch {
 };
 int launch_fused2d(const Fused2DLaunch &L);
 size_t fused2d_smem_bytes(int tile_x, int tile_y, int radius, int steps);
+
+// Variable-coefficient sweeps (VAR forward/adjoint, div(k grad u)).
+struct VarLaunch {
+    int ndim;
+    int64_t nz, ny, nx;
+    int shape, radius, dtype;
+    int periodic;
+    const void *in;
+    void *out;
+    const void *const *arrays;  // VAR: npts arrays; DIVKGRAD: k
+    int narrays;
+    int block_y, z_chunk;
+    cudaStream_t stream;
+};
+#define GST_DECLARE_VAR(DT)                               \
+    int launch_var_##DT##_fwd(const VarLaunch &L);        \
+    int launch_var_##DT##_adj(const VarLaunch &L);        \
+    int launch_divkgrad_##DT(const VarLaunch &L);
+GST_DECLARE_VAR(f32)
+GST_DECLARE_VAR(f16)
+GST_DECLARE_VAR(bf16)
+#undef GST_DECLARE_VAR
+constexpr int kMaxVarArrays = 27;
 
 // Kernel launch counter (all families).
 void count_launch(uint64_t n = 1);

@@ -3,13 +3,6 @@
 #include "../../include/stencil.h"
 
 extern "C" {
-int stencil_apply_var(stencil_handle, const void *, const void *const *, void *, int, void *) {
-    return STENCIL_ERR_UNSUPPORTED;
-}
-int stencil_apply_adjoint_var(stencil_handle, const void *, const void *const *, void *, int,
-                              void *) {
-    return STENCIL_ERR_UNSUPPORTED;
-}
 int stencil_batch_plan(stencil_batch *out, const stencil_batch_item *, int, int) {
     if (out) *out = nullptr;
     return STENCIL_ERR_UNSUPPORTED;

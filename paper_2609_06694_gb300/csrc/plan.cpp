@@ -74,7 +74,7 @@ static stencil_variant default_variant(const stencil_plan_s &p) {
     v.block_x = 128 / vx;  // 128-cell tiles in x
     v.block_y = 256 / v.block_x;
     v.vec_y = 1;
-    v.z_chunk = p.ndim == 3 ? 64 : 0;
+    v.z_chunk = p.ndim == 3 ? 128 : 0;
     v.fuse = 1;
     if (p.ndim == 3) {
         // two rows per thread while the partial-sum queue stays small
@@ -117,8 +117,9 @@ static bool lookup_map(const stencil_plan_s &p, stencil_variant *out) {
 
 int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
     if (v.family == STENCIL_FAMILY_STREAM) {
-        if (v.block_x < 1 || v.block_y < 1 || v.block_x * v.block_y > 256 ||
-            (v.block_x * v.block_y) % 32 != 0)
+        // tiles are 128 cells wide: one 16-byte vector of cells per thread along x
+        if (v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
+            v.block_x * v.block_y > 256 || (v.block_x * v.block_y) % 32 != 0)
             return STENCIL_ERR_BADARG;
         if (!stream_vy_compiled(p.ndim, p.shape, p.radius, v.vec_y))
             return STENCIL_ERR_UNSUPPORTED;
@@ -139,7 +140,7 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
 
 static int cuda_status(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ERR_CUDA; }
 
-static int map_launch_rc(int rc) {
+int map_launch_rc(int rc) {
     if (rc == 0) return STENCIL_OK;
     if (rc == -1) return STENCIL_ERR_BADARG;
     if (rc == -2) return STENCIL_ERR_UNSUPPORTED;
@@ -228,7 +229,7 @@ int run_steps(stencil_plan_s &p, const float *cf, const void *in, void *out, int
     return STENCIL_OK;
 }
 
-static bool overlaps(const void *a, const void *b, size_t n) {
+bool overlaps(const void *a, const void *b, size_t n) {
     uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
     return x < y + n && y < x + n;
 }
@@ -461,6 +462,69 @@ int stencil_load_dispatch_map(const char *path) {
 
 namespace gst {
 
+// Variable-coefficient sweeps: `steps` launches ping-ponging through out and the scratch grid.
+static int run_var_steps(stencil_plan_s &p, const void *in, const void *const *arrays,
+                         void *out, int steps, bool adjoint, cudaStream_t s) {
+    if (steps > 1) {
+        int rc = ensure_scratch(p);
+        if (rc) return rc;
+    }
+    VarLaunch L;
+    L.ndim = p.ndim;
+    L.nz = p.dims[0];
+    L.ny = p.dims[1];
+    L.nx = p.dims[2];
+    L.shape = p.shape;
+    L.radius = p.radius;
+    L.dtype = p.dtype;
+    L.periodic = p.boundary == STENCIL_PERIODIC;
+    L.arrays = arrays;
+    L.narrays = p.kind == STENCIL_DIVKGRAD ? 1 : (int)p.npts;
+    L.block_y = 8;
+    L.z_chunk = 64;
+    L.stream = s;
+    const void *src = in;
+    for (int g = 0; g < steps; ++g) {
+        void *dst = ((steps - 1 - g) % 2 == 0) ? out : p.scratch;
+        L.in = src;
+        L.out = dst;
+        int rc;
+        if (p.kind == STENCIL_DIVKGRAD) {
+            // the operator is symmetric: its adjoint is itself
+            rc = p.dtype == STENCIL_F32   ? launch_divkgrad_f32(L)
+                 : p.dtype == STENCIL_F16 ? launch_divkgrad_f16(L)
+                                          : launch_divkgrad_bf16(L);
+        } else if (!adjoint) {
+            rc = p.dtype == STENCIL_F32   ? launch_var_f32_fwd(L)
+                 : p.dtype == STENCIL_F16 ? launch_var_f16_fwd(L)
+                                          : launch_var_bf16_fwd(L);
+        } else {
+            rc = p.dtype == STENCIL_F32   ? launch_var_f32_adj(L)
+                 : p.dtype == STENCIL_F16 ? launch_var_f16_adj(L)
+                                          : launch_var_bf16_adj(L);
+        }
+        if (rc) return map_launch_rc(rc);
+        src = dst;
+    }
+    return STENCIL_OK;
+}
+
+static int apply_var_common(stencil_handle h, const void *in, const void *const *arrays,
+                            void *out, int steps, void *stream, bool adjoint) {
+    int rc = check_apply_args(h, in, out, steps);
+    if (rc) return rc;
+    if (h->kind != STENCIL_VAR && h->kind != STENCIL_DIVKGRAD) return STENCIL_ERR_BADARG;
+    if (!arrays) return STENCIL_ERR_BADARG;
+    const int n = h->kind == STENCIL_DIVKGRAD ? 1 : (int)h->npts;
+    if (n > kMaxVarArrays) return STENCIL_ERR_UNSUPPORTED;
+    const size_t bytes = (size_t)h->dims[0] * h->dims[1] * h->dims[2] * dtype_size(h->dtype);
+    for (int i = 0; i < n; ++i) {
+        if (!arrays[i]) return STENCIL_ERR_BADARG;
+        if (overlaps(arrays[i], out, bytes)) return STENCIL_ERR_BADARG;
+    }
+    return run_var_steps(*h, in, arrays, out, steps, adjoint, (cudaStream_t)stream);
+}
+
 int launch_stream(const StreamLaunch &L) {
 #define GST_CASE(DT, ND)                                                  \
     if (L.ndim == ND) {                                                   \
@@ -482,3 +546,17 @@ int launch_stream(const StreamLaunch &L) {
 }
 
 }  // namespace gst
+
+extern "C" {
+
+int stencil_apply_var(stencil_handle h, const void *in, const void *const *coeff_arrays,
+                      void *out, int steps, void *stream) {
+    return gst::apply_var_common(h, in, coeff_arrays, out, steps, stream, false);
+}
+
+int stencil_apply_adjoint_var(stencil_handle h, const void *in, const void *const *coeff_arrays,
+                              void *out, int steps, void *stream) {
+    return gst::apply_var_common(h, in, coeff_arrays, out, steps, stream, true);
+}
+
+}  // extern "C"

@@ -34,4 +34,6 @@ int ensure_scratch(stencil_plan_s &p);
 int run_steps(stencil_plan_s &p, const float *cf, const void *in, void *out, int steps,
               cudaStream_t s);
 int check_apply_args(const stencil_plan_s *p, const void *in, const void *out, int steps);
+bool overlaps(const void *a, const void *b, size_t n);
+int map_launch_rc(int rc);
 }  // namespace gst

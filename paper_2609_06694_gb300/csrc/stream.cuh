@@ -32,6 +32,22 @@ template <int N, typename F> __device__ __forceinline__ void static_for(F &&f) {
     static_for_impl<N>(f, std::make_integer_sequence<int, N>{});
 }
 
+// Calls f(integral_constant<k>) for the runtime value ph in [0, P), P <= 9, via a switch.
+template <int P, typename F> __device__ __forceinline__ void phase_switch(int ph, F &&f) {
+    static_assert(P <= 9, "phase_switch handles up to 9 phases");
+    switch (ph) {
+#define GST_PHASE_CASE(k)                                                 \
+    case k:                                                               \
+        if constexpr (k < P) f(std::integral_constant<int, k>{});         \
+        break;
+        GST_PHASE_CASE(0) GST_PHASE_CASE(1) GST_PHASE_CASE(2) GST_PHASE_CASE(3)
+        GST_PHASE_CASE(4) GST_PHASE_CASE(5) GST_PHASE_CASE(6) GST_PHASE_CASE(7)
+        GST_PHASE_CASE(8)
+#undef GST_PHASE_CASE
+    default: break;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Loads of a compile-time element range [LO, HI) from a 16-byte-aligned shared-memory base,
 // converted to float into dst[(e - LO0)] where LO0 is the window origin.
@@ -107,117 +123,154 @@ template <typename T> struct StreamParams {
     int *err;           // device error word (may be null)
 };
 
-// Ordinary output: round to the storage type and store.
-struct PlainStore {};
+// How the partial-sum queue is indexed:
+//  kQueueUnrolled : the z loop is unrolled by 2R+1 so every queue index is a constant;
+//  kQueueRotate   : the queue is shifted by one entry after every plane (large stencils);
+//  kQueueStarSplit: stars only -- the in-plane cross goes to a temporary, and a switch on
+//                   the plane's phase adds it and the 2R single-point z terms to the queue.
+enum QueueMode : int { kQueueUnrolled = 0, kQueueRotate = 1, kQueueStarSplit = 2 };
 
-// ---------------------------------------------------------------------------------------
-// The kernel
-// ---------------------------------------------------------------------------------------
-template <typename T, int NDIM, int SHAPE, int R, int VX, int VY, int NSTAGE, bool UNROLLZ>
+template <typename T, int NDIM, int SHAPE, int R, int VY, int NSTAGE, int QMODE>
 struct StreamKernel {
     static constexpr int RZ = (NDIM == 3) ? R : 0;
     static constexpr int P = 2 * RZ + 1;
-    static constexpr int A = 16 / (int)sizeof(T);  // x halo: one 16-byte chunk
+    static constexpr int VX = 16 / (int)sizeof(T);  // one 16-byte vector of cells per row
+    static constexpr int A = VX;                     // x halo: one 16-byte chunk
+    static constexpr int TX = 128;                   // tile width (cells)
+    static constexpr int BX = TX / VX;               // threads along x
+    static constexpr int PITCH = TX + 2 * A;         // shared-memory row length (elements)
     using OT = OffsetTable<NDIM, SHAPE, R>;
     static constexpr int NPTS = OT::count;
-    static constexpr int KMAX = 4;                  // per-thread chunk slots (loader)
+    static constexpr int KMAX = 4;                   // per-thread chunk slots (loader)
+    static constexpr bool CREG = NPTS <= 32;         // coefficients held in registers
     static_assert(R <= A, "x halo must fit in one 16-byte chunk");
-    static_assert((VX * (int)sizeof(T)) % 16 == 0, "VX cells must span whole 16-byte chunks");
+    static_assert(QMODE != kQueueStarSplit || SHAPE == kStar, "split mode is for stars");
 
     // needed |dx| for window row wr (union over the thread's rows and every dz); -1 = unused
-    __host__ __device__ static constexpr int row_m(int wr) {
+    __host__ __device__ static constexpr int row_m(int wr, bool inplane_only) {
         int m = -1;
         for (int vy = 0; vy < VY; ++vy) {
             int dy = wr - R - vy;
             if (dy < -R || dy > R) continue;
-            int v = OT::max_dx_any(dy);
+            int v = inplane_only ? OT::tab.mdx[R][dy + R] : OT::max_dx_any(dy);
             if (v > m) m = v;
         }
         return m;
     }
 
-    static size_t smem_bytes(int bx, int by) {
-        int pitch = bx * VX + 2 * A;
-        int rows = by * VY + 2 * R;
-        return (size_t)NSTAGE * pitch * rows * sizeof(T);
+    static size_t smem_bytes(int by) {
+        return (size_t)NSTAGE * PITCH * (by * VY + 2 * R) * sizeof(T);
     }
 };
 
-template <typename T, int NDIM, int SHAPE, int R, int VX, int VY, int NSTAGE, bool UNROLLZ>
+template <typename T, int NDIM, int SHAPE, int R, int VY, int NSTAGE, int QMODE>
 __global__ void __launch_bounds__(256)
     stream_sweep_kernel(const StreamParams<T> p,
                         const __grid_constant__ ConstCoeffs<OffsetTable<NDIM, SHAPE, R>::count> cf) {
-    using K = StreamKernel<T, NDIM, SHAPE, R, VX, VY, NSTAGE, UNROLLZ>;
-    constexpr int RZ = K::RZ, P = K::P, A = K::A;
+    using K = StreamKernel<T, NDIM, SHAPE, R, VY, NSTAGE, QMODE>;
+    constexpr int RZ = K::RZ, P = K::P, A = K::A, VX = K::VX, PITCH = K::PITCH, TX = K::TX;
+    constexpr int ES = (int)sizeof(T);
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *smem = reinterpret_cast<T *>(smem_raw);
 
-    const int bx = blockDim.x, by = blockDim.y;
+    const int by = blockDim.y;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * bx + tx, nthr = bx * by;
-    const int TX = bx * VX, TY = by * VY;
-    const int pitch = TX + 2 * A;
+    const int tid = ty * K::BX + tx, nthr = K::BX * by;
+    const int TY = by * VY;
     const int rows = TY + 2 * R;
-    const int plane_elems = pitch * rows;
+    const int plane_elems = PITCH * rows;
 
     int b = blockIdx.x;
     const int tix = b % p.tiles_x;
     b /= p.tiles_x;
     const int tiy = b % p.tiles_y;
     const int tiz = b / p.tiles_y;
+    const int nx = p.nx, ny = p.ny;
     const int x0 = tix * TX, y0 = tiy * TY;
     const int z_begin = (NDIM == 3) ? tiz * p.zchunk : 0;
     const int z_end = (NDIM == 3) ? min(p.nz, z_begin + p.zchunk) : 1;
     const int zs = z_begin - RZ, zl = z_end + RZ;
     const bool periodic = p.periodic != 0;
-    const size_t plane_stride = (size_t)p.nx * p.ny;
+    const bool aligned = p.aligned != 0;
+    const size_t plane_stride = (size_t)nx * ny;
 
-    // ---- per-thread loader slots (aligned path): smem offset and in-plane source offset ----
-    const int cpr = pitch / A;
-    const int nchunks = cpr * rows;
-    int ld_dst[K::KMAX], ld_src[K::KMAX];
+    // coefficients: registers for small stencils, the parameter bank otherwise
+    float creg[K::CREG ? K::NPTS : 1];
+    if constexpr (K::CREG) {
+#pragma unroll
+        for (int i = 0; i < K::NPTS; ++i) creg[i] = cf.c[i];
+    }
+    auto coef = [&](auto idx_c) -> float {
+        constexpr int idx = decltype(idx_c)::value;
+        if constexpr (K::CREG) return creg[idx];
+        else return cf.c[idx];
+    };
+
+    // ---- per-thread loader slots (aligned path): smem byte offset and in-plane source ----
+    constexpr int CPR = PITCH / A;
+    const int nchunks = CPR * rows;
+    const uint32_t smem_u32 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    uint32_t ld_dst[K::KMAX];
+    int ld_src[K::KMAX];
+    int nk = 0;
 #pragma unroll
     for (int k = 0; k < K::KMAX; ++k) {
-        int c = tid + k * nthr;
-        ld_dst[k] = -1;
+        const int c = tid + k * nthr;
+        ld_dst[k] = 0;
         ld_src[k] = -1;
-        if (k < p.kchunks && c < nchunks) {
-            int row = c / cpr, cc = c - row * cpr;
+        if (c < nchunks) {
+            const int row = c / CPR, cc = c - row * CPR;
             bool ok = true;
-            int gy = wrap_or_flag(y0 - R + row, p.ny, periodic, ok);
-            int gx = wrap_or_flag(x0 - A + cc * A, p.nx, periodic, ok);
-            ld_dst[k] = row * pitch + cc * A;
-            ld_src[k] = ok ? gy * p.nx + gx : -1;
+            const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
+            const int gx = wrap_or_flag(x0 - A + cc * A, nx, periodic, ok);
+            ld_dst[k] = (uint32_t)(c * 16);  // chunk c of the row-major tile is bytes 16c..
+            ld_src[k] = ok ? gy * nx + gx : -1;
+            nk = k + 1;
         }
     }
 
     auto load_plane = [&](int zi, int slot) {
         bool zok = true;
-        int gz = (NDIM == 3) ? wrap_or_flag(zi, p.nz, periodic, zok) : 0;
+        const int gz = (NDIM == 3) ? wrap_or_flag(zi, p.nz, periodic, zok) : 0;
         const T *plane = p.in + (size_t)gz * plane_stride;
-        T *dst = smem + slot * plane_elems;
-        if (p.aligned) {
+        if (aligned) {
+            const uint32_t sbase = smem_u32 + (uint32_t)(slot * plane_elems * ES);
 #pragma unroll
             for (int k = 0; k < K::KMAX; ++k) {
-                if (ld_dst[k] >= 0) {
-                    bool ok = zok && ld_src[k] >= 0;
-                    cp_async16(dst + ld_dst[k], ok ? (const void *)(plane + ld_src[k])
-                                                   : (const void *)p.in,
-                               ok ? 16 : 0);
+                if (k < nk) {
+                    const bool ok = zok && ld_src[k] >= 0;
+                    const T *src = ok ? plane + ld_src[k] : p.in;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                                     sbase + ld_dst[k]),
+                                 "l"(src), "r"(ok ? 16 : 0)
+                                 : "memory");
                 }
+            }
+            // chunks beyond the register slots: address computed on the fly
+            for (int c = tid + K::KMAX * nthr; c < nchunks; c += nthr) {
+                const int row = c / CPR, cc = c - row * CPR;
+                bool ok = zok;
+                const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
+                const int gx = wrap_or_flag(x0 - A + cc * A, nx, periodic, ok);
+                const T *src = ok ? plane + gy * nx + gx : p.in;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                                 sbase + (uint32_t)(c * 16)),
+                             "l"(src), "r"(ok ? 16 : 0)
+                             : "memory");
             }
         } else {
             // scalar path: only the cells the stencil reads (x0-R .. x0+TX+R)
+            T *dst = smem + slot * plane_elems;
             const int wcols = TX + 2 * R;
             const int n = wcols * rows;
             for (int e = tid; e < n; e += nthr) {
-                int row = e / wcols, col = e - row * wcols;
+                const int row = e / wcols, col = e - row * wcols;
                 bool ok = zok;
-                int gy = wrap_or_flag(y0 - R + row, p.ny, periodic, ok);
-                int gx = wrap_or_flag(x0 - R + col, p.nx, periodic, ok);
-                T v = ok ? plane[(size_t)gy * p.nx + gx] : Storage<T>::from_float(0.0f);
-                dst[row * pitch + (A - R) + col] = v;
+                const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
+                const int gx = wrap_or_flag(x0 - R + col, nx, periodic, ok);
+                const T v = ok ? plane[(size_t)gy * nx + gx] : Storage<T>::from_float(0.0f);
+                dst[row * PITCH + (A - R) + col] = v;
             }
         }
     };
@@ -237,36 +290,66 @@ __global__ void __launch_bounds__(256)
         cp_async_commit();
     }
 
-    const int ox = x0 + tx * VX;  // first owned column
-    const int oy = y0 + ty * VY;  // first owned row
+    // output addressing, hoisted
+    const int ox = x0 + tx * VX;
+    const int oy = y0 + ty * VY;
+    T *const obase = p.out + (size_t)oy * nx + ox;
+    const bool xfull = aligned && (ox + VX <= nx);
+    const int vy_valid = min(VY, ny - oy);  // may be <= 0
+    const int thr_off = (ty * VY) * PITCH + A + tx * VX;  // element offset of the thread's base
 
-    // accumulate the contributions of the plane in `slot` to the queued outputs; JOF(dz) is
-    // the queue index of output (zi - dz)
-    auto accumulate = [&](const T *plane_smem, auto jof) {
-        const T *tbase = plane_smem + (ty * VY) * pitch + A + tx * VX;
+    auto store_output = [&](int zo, const float (&vals)[VY][VX]) {
+        if (zo < z_begin || zo >= z_end) return;
+        T *orow = obase + (size_t)zo * plane_stride;
+#pragma unroll
+        for (int vy = 0; vy < VY; ++vy) {
+            if (vy >= vy_valid) break;
+            T *dst = orow + (size_t)vy * nx;
+            if (xfull) {
+                T tmp[VX];
+#pragma unroll
+                for (int vx = 0; vx < VX; ++vx) tmp[vx] = Storage<T>::from_float(vals[vy][vx]);
+                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tmp);
+            } else {
+#pragma unroll
+                for (int vx = 0; vx < VX; ++vx)
+                    if (ox + vx < nx) dst[vx] = Storage<T>::from_float(vals[vy][vx]);
+            }
+        }
+    };
+
+    // add the in-plane slice(s) of the plane at `tb` to the queue; JOF(dz) = queue index of
+    // output (zi - dz).  INPLANE_ONLY restricts to dz = 0 and writes into `tmp` instead.
+    auto accumulate = [&](const T *tb, auto jof, auto inplane_only_c, float (&tmp)[VY][VX]) {
+        constexpr bool IPO = decltype(inplane_only_c)::value;
         static_for<VY + 2 * R>([&](auto wr_c) {
             constexpr int wr = decltype(wr_c)::value;
-            constexpr int m = K::row_m(wr);
+            constexpr int m = K::row_m(wr, IPO);
             if constexpr (m >= 0) {
                 float win[VX + 2 * R];
-                load_span<T, -m, VX + m, -R>(tbase + wr * pitch, win);
+                load_span<T, -m, VX + m, -R>(tb + wr * PITCH, win);
                 static_for<VY>([&](auto vy_c) {
                     constexpr int vy = decltype(vy_c)::value;
                     constexpr int dy = wr - R - vy;
                     if constexpr (dy >= -R && dy <= R) {
                         static_for<P>([&](auto dzi_c) {
                             constexpr int dz = decltype(dzi_c)::value - RZ;
-                            constexpr int j = decltype(jof(std::integral_constant<int, dz>{}))::value;
-                            static_for<2 * R + 1>([&](auto dxi_c) {
-                                constexpr int dx = decltype(dxi_c)::value - R;
-                                constexpr int idx = K::OT::index(dz, dy, dx);
-                                if constexpr (idx >= 0) {
-                                    const float c = cf.c[idx];
+                            if constexpr (!IPO || dz == 0) {
+                                constexpr int j =
+                                    decltype(jof(std::integral_constant<int, dz>{}))::value;
+                                static_for<2 * R + 1>([&](auto dxi_c) {
+                                    constexpr int dx = decltype(dxi_c)::value - R;
+                                    constexpr int idx = K::OT::index(dz, dy, dx);
+                                    if constexpr (idx >= 0) {
+                                        const float c = coef(std::integral_constant<int, idx>{});
 #pragma unroll
-                                    for (int vx = 0; vx < VX; ++vx)
-                                        acc[j][vy][vx] = fmaf(c, win[vx + dx + R], acc[j][vy][vx]);
-                                }
-                            });
+                                        for (int vx = 0; vx < VX; ++vx) {
+                                            float &dst = IPO ? tmp[vy][vx] : acc[j][vy][vx];
+                                            dst = fmaf(c, win[vx + dx + R], dst);
+                                        }
+                                    }
+                                });
+                            }
                         });
                     }
                 });
@@ -274,85 +357,109 @@ __global__ void __launch_bounds__(256)
         });
     };
 
-    auto store_output = [&](int zo, float (&vals)[VY][VX]) {
-        if (zo < z_begin || zo >= z_end) return;
-        T *orow0 = p.out + (size_t)zo * plane_stride;
+    auto zero_slot = [&](float (&a)[VY][VX]) {
 #pragma unroll
-        for (int vy = 0; vy < VY; ++vy) {
-            const int y = oy + vy;
-            if (y >= p.ny) continue;
-            T *dst = orow0 + (size_t)y * p.nx + ox;
-            if (p.aligned && ox + VX <= p.nx) {
-                T tmp[VX];
+        for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                for (int vx = 0; vx < VX; ++vx) tmp[vx] = Storage<T>::from_float(vals[vy][vx]);
-#pragma unroll
-                for (int q = 0; q < (VX * (int)sizeof(T)) / 16; ++q)
-                    reinterpret_cast<uint4 *>(dst)[q] = reinterpret_cast<const uint4 *>(tmp)[q];
-            } else {
-#pragma unroll
-                for (int vx = 0; vx < VX; ++vx)
-                    if (ox + vx < p.nx) dst[vx] = Storage<T>::from_float(vals[vy][vx]);
-            }
-        }
+            for (int vx = 0; vx < VX; ++vx) a[vy][vx] = 0.0f;
+    };
+
+    // one plane: wait for it, keep the ring full, consume it
+    auto begin_plane = [&](int zi, int slot) -> const T * {
+        cp_async_wait<NSTAGE - 2>();
+        __syncthreads();
+        const int zn = zi + NSTAGE - 1;
+        int sn = slot + NSTAGE - 1;
+        if (sn >= NSTAGE) sn -= NSTAGE;
+        if (zn < zl) load_plane(zn, sn);
+        cp_async_commit();
+        return smem + slot * plane_elems + thr_off;
     };
 
     int zi = zs;
     int slot = 0;
-    constexpr int PU = UNROLLZ ? P : 1;
-    bool done = false;
-    while (!done) {
-        static_for<PU>([&](auto ph_c) {
-            constexpr int ph = decltype(ph_c)::value;
-            (void)ph;
-            if (done) return;
-            if (zi >= zl) {
-                done = true;
-                return;
-            }
-            cp_async_wait<NSTAGE - 2>();
-            __syncthreads();
-            {
-                const int zn = zi + NSTAGE - 1;
-                int sn = slot + NSTAGE - 1;
-                if (sn >= NSTAGE) sn -= NSTAGE;
-                if (zn < zl) load_plane(zn, sn);
-                cp_async_commit();
-            }
-            const T *pl = smem + slot * plane_elems;
-            if constexpr (UNROLLZ) {
-                // queue index of output (zi - dz) is (ph - dz) mod P
-                accumulate(pl, [](auto dz_c) {
+    float dummy[VY][VX];
+    if constexpr (QMODE == kQueueUnrolled) {
+        bool done = false;
+        while (!done) {
+            static_for<P>([&](auto ph_c) {
+                constexpr int ph = decltype(ph_c)::value;
+                if (done) return;
+                if (zi >= zl) {
+                    done = true;
+                    return;
+                }
+                const T *tb = begin_plane(zi, slot);
+                accumulate(tb, [](auto dz_c) {
                     constexpr int dz = decltype(dz_c)::value;
                     return std::integral_constant<int, imod_c(ph - dz, P)>{};
-                });
+                }, std::false_type{}, dummy);
                 constexpr int jo = imod_c(ph - RZ, P);
                 store_output(zi - RZ, acc[jo]);
+                zero_slot(acc[jo]);
+                ++zi;
+                slot = (slot + 1 == NSTAGE) ? 0 : slot + 1;
+            });
+        }
+    } else if constexpr (QMODE == kQueueRotate) {
+        for (; zi < zl; ++zi) {
+            const T *tb = begin_plane(zi, slot);
+            accumulate(tb, [](auto dz_c) {
+                constexpr int dz = decltype(dz_c)::value;
+                return std::integral_constant<int, RZ - dz>{};
+            }, std::false_type{}, dummy);
+            store_output(zi - RZ, acc[0]);
+#pragma unroll
+            for (int j = 0; j + 1 < P; ++j)
 #pragma unroll
                 for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                    for (int vx = 0; vx < VX; ++vx) acc[jo][vy][vx] = 0.0f;
-            } else {
-                // queue index j holds output zi - RZ + j
-                accumulate(pl, [](auto dz_c) {
-                    constexpr int dz = decltype(dz_c)::value;
-                    return std::integral_constant<int, RZ - dz>{};
-                });
-                store_output(zi - RZ, acc[0]);
+                    for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] = acc[j + 1][vy][vx];
+            zero_slot(acc[P - 1]);
+            slot = (slot + 1 == NSTAGE) ? 0 : slot + 1;
+        }
+    } else {
+        // star split: in-plane cross into tmp, then a phase switch for the z line
+        int ph = 0;
+        for (; zi < zl; ++zi) {
+            const T *tb = begin_plane(zi, slot);
+            float tmp[VY][VX];
+            zero_slot(tmp);
+            accumulate(tb, [](auto) { return std::integral_constant<int, 0>{}; },
+                       std::true_type{}, tmp);
+            // centre values of this plane (the z-line terms read them)
+            float ctr[VY][VX];
 #pragma unroll
-                for (int j = 0; j + 1 < P; ++j)
+            for (int vy = 0; vy < VY; ++vy) {
+                float w[VX];
+                load_span<T, 0, VX, 0>(tb + (vy + R) * PITCH, w);
+#pragma unroll
+                for (int vx = 0; vx < VX; ++vx) ctr[vy][vx] = w[vx];
+            }
+            phase_switch<P>(ph, [&](auto ph_c) {
+                constexpr int PH = decltype(ph_c)::value;
+                static_for<P>([&](auto dzi_c) {
+                    constexpr int dz = decltype(dzi_c)::value - RZ;
+                    constexpr int j = imod_c(PH - dz, P);
 #pragma unroll
                     for (int vy = 0; vy < VY; ++vy)
 #pragma unroll
-                        for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] = acc[j + 1][vy][vx];
-#pragma unroll
-                for (int vy = 0; vy < VY; ++vy)
-#pragma unroll
-                    for (int vx = 0; vx < VX; ++vx) acc[P - 1][vy][vx] = 0.0f;
-            }
-            ++zi;
+                        for (int vx = 0; vx < VX; ++vx) {
+                            if constexpr (dz == 0)
+                                acc[j][vy][vx] += tmp[vy][vx];
+                            else
+                                acc[j][vy][vx] = fmaf(
+                                    coef(std::integral_constant<int, K::OT::index(dz, 0, 0)>{}),
+                                    ctr[vy][vx], acc[j][vy][vx]);
+                        }
+                });
+                constexpr int jo = imod_c(PH - RZ, P);
+                store_output(zi - RZ, acc[jo]);
+                zero_slot(acc[jo]);
+            });
+            ph = (ph + 1 == P) ? 0 : ph + 1;
             slot = (slot + 1 == NSTAGE) ? 0 : slot + 1;
-        });
+        }
     }
     cp_async_wait<0>();
 }

@@ -8,25 +8,27 @@
 
 namespace gst {
 
-// The z loop is unrolled by 2R+1 (queue indices become constants) only while the unrolled
-// body stays small; larger stencils rotate their partial-sum queue instead.
-constexpr bool stream_unroll_z(int ndim, int shape, int r, int vx, int vy) {
-    return ndim == 2 || shape_count(ndim, shape, r) * vx * vy * (2 * r + 1) <= 2000;
+// Queue mode: 3D stars split off their in-plane cross; other small stencils unroll the z loop
+// by 2R+1 while the unrolled body stays small; larger ones rotate their partial-sum queue.
+constexpr int stream_queue_mode(int ndim, int shape, int r, int vx, int vy) {
+    if (ndim == 3 && shape == kStar) return kQueueStarSplit;
+    if (ndim == 2 || shape_count(ndim, shape, r) * vx * vy * (2 * r + 1) <= 2000)
+        return kQueueUnrolled;
+    return kQueueRotate;
 }
 
 template <typename T, int NDIM, int SHAPE, int R, int VY>
 int launch_stream_t(const StreamLaunch &L) {
-    constexpr int VX = 16 / (int)sizeof(T);  // one 16-byte vector of cells per thread row
-    constexpr int NSTAGE = 3;
+    constexpr int VX = 16 / (int)sizeof(T);
+    constexpr int NSTAGE = NDIM == 3 ? 4 : 2;  // 2D grids load a single plane
     constexpr int NPTS = OffsetTable<NDIM, SHAPE, R>::count;
-    constexpr int P = NDIM == 3 ? 2 * R + 1 : 1;
-    constexpr bool UNROLLZ = stream_unroll_z(NDIM, SHAPE, R, VX, VY);
-    using K = StreamKernel<T, NDIM, SHAPE, R, VX, VY, NSTAGE, UNROLLZ>;
-    auto kern = stream_sweep_kernel<T, NDIM, SHAPE, R, VX, VY, NSTAGE, UNROLLZ>;
+    constexpr int QM = stream_queue_mode(NDIM, SHAPE, R, VX, VY);
+    using K = StreamKernel<T, NDIM, SHAPE, R, VY, NSTAGE, QM>;
+    auto kern = stream_sweep_kernel<T, NDIM, SHAPE, R, VY, NSTAGE, QM>;
 
-    const int bx = L.block_x, by = L.block_y;
-    if (bx < 1 || by < 1 || bx * by > 256 || bx * by % 32 != 0) return -1;
-    const int TX = bx * VX, TY = by * VY;
+    const int by = L.block_y;
+    if (L.block_x != K::BX || by < 1 || K::BX * by > 256 || (K::BX * by) % 32 != 0) return -1;
+    const int TX = K::TX, TY = by * VY;
     const int64_t nx = L.nx, ny = L.ny, nz = NDIM == 3 ? L.nz : 1;
     if (nx * ny > (int64_t)INT32_MAX - 4 * TX) return -2;
 
@@ -42,12 +44,11 @@ int launch_stream_t(const StreamLaunch &L) {
     const int zc = (NDIM == 3 && L.z_chunk > 0) ? L.z_chunk : (int)nz;
     p.zchunk = zc;
     const int64_t zchunks = NDIM == 3 ? (nz + zc - 1) / zc : 1;
-    const int pitch = TX + 2 * K::A;
     const int rows = TY + 2 * R;
-    const int nchunks = (pitch / K::A) * rows;
-    p.kchunks = (nchunks + bx * by - 1) / (bx * by);
+    const int nchunks = (K::PITCH / K::A) * rows;
+    p.kchunks = (nchunks + K::BX * by - 1) / (K::BX * by);
     const bool ptr_ok = ((uintptr_t)L.in % 16 == 0) && ((uintptr_t)L.out % 16 == 0);
-    p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0 && p.kchunks <= K::KMAX) ? 1 : 0;
+    p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
     p.err = L.err;
 
     ConstCoeffs<NPTS> cf;
@@ -55,7 +56,7 @@ int launch_stream_t(const StreamLaunch &L) {
 
     const int64_t nblocks = (int64_t)p.tiles_x * p.tiles_y * zchunks;
     if (nblocks > INT32_MAX) return -2;
-    const size_t smem = K::smem_bytes(bx, by);
+    const size_t smem = K::smem_bytes(by);
     static size_t smem_set = 0;  // per instantiation
     if (smem > 48 * 1024 && smem > smem_set) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -63,7 +64,7 @@ int launch_stream_t(const StreamLaunch &L) {
             return -4;
         smem_set = smem;
     }
-    kern<<<(unsigned)nblocks, dim3(bx, by), smem, L.stream>>>(p, cf);
+    kern<<<(unsigned)nblocks, dim3(K::BX, by), smem, L.stream>>>(p, cf);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
 }
@@ -72,6 +73,9 @@ template <typename T, int NDIM, int SHAPE, int R> int launch_stream_vy(const Str
     if (L.vec_y == 1) return launch_stream_t<T, NDIM, SHAPE, R, 1>(L);
     if constexpr (stream_vy_compiled(NDIM, SHAPE, R, 2)) {
         if (L.vec_y == 2) return launch_stream_t<T, NDIM, SHAPE, R, 2>(L);
+    }
+    if constexpr (stream_vy_compiled(NDIM, SHAPE, R, 4)) {
+        if (L.vec_y == 4) return launch_stream_t<T, NDIM, SHAPE, R, 4>(L);
     }
     return -2;
 }

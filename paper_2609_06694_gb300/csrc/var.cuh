@@ -1,0 +1,316 @@
+// Variable-coefficient sweeps (ForgeStencil Sec. 2.1: coefficients that vary in space are one
+// more array per offset):
+//   forward   out[p] = sum_o w_o[p]   * in[p + o]
+//   adjoint   out[q] = sum_o w_o[q-o] * in[q - o]      (offset flipped, coefficient gathered
+//                                                      at the shifted cell)
+//   div(k grad u), unit spacing, conservative star-1 form with face k = mean of the two cells.
+//
+// Design: a CTA owns a 128-cell x TY tile and walks z.  The 2R+1 input planes an output plane
+// needs (plus one in flight) sit in a ring of shared-memory slots filled by 16-byte cp.async
+// (zero fill = Dirichlet ghosts, wrapped addresses = periodic), so each output is computed
+// in one pass with a single FP32 accumulator; coefficient arrays are read straight from
+// global memory (each value is used once, so staging would not save traffic).
+#pragma once
+
+#include "common.cuh"
+#include "stream.cuh"
+
+namespace gst {
+
+constexpr int kMaxVarPts = 27;  // coefficient arrays per VAR plan (3D box r1 has 27)
+
+template <typename T> struct VarParams {
+    const T *in;
+    T *out;
+    const T *w[kMaxVarPts];  // VAR: one array per offset (canonical order); DIVKGRAD: w[0] = k
+    int nx, ny, nz;
+    int periodic;
+    int aligned;
+    int tiles_x, tiles_y, zchunk;
+};
+
+// Copies one plane tile (rows y0-R .. y0+TY+R-1, 16-byte chunks x0-A .. x0+TX+A-1) into a
+// shared-memory slot: cp.async when rows are 16-byte aligned, element loads otherwise.
+template <typename T, int R, int A, int PITCH>
+__device__ __forceinline__ void load_tile_plane(const T *__restrict__ field, T *slot_smem, int zi,
+                                                int nx, int ny, int nz, bool periodic,
+                                                bool aligned, int x0, int y0, int rows, int tid,
+                                                int nthr, bool is3d) {
+    bool zok = true;
+    const int gz = is3d ? wrap_or_flag(zi, nz, periodic, zok) : 0;
+    const T *plane = field + (size_t)gz * nx * ny;
+    constexpr int CPR = PITCH / A;
+    if (aligned) {
+        const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(slot_smem));
+        const int nchunks = CPR * rows;
+        for (int c = tid; c < nchunks; c += nthr) {
+            const int row = c / CPR, cc = c - row * CPR;
+            bool ok = zok;
+            const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
+            const int gx = wrap_or_flag(x0 - A + cc * A, nx, periodic, ok);
+            const T *src = ok ? plane + (size_t)gy * nx + gx : field;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sbase + c * 16),
+                         "l"(src), "r"(ok ? 16 : 0)
+                         : "memory");
+        }
+    } else {
+        const int wcols = PITCH - 2 * A + 2 * R;
+        const int n = wcols * rows;
+        for (int e = tid; e < n; e += nthr) {
+            const int row = e / wcols, col = e - row * wcols;
+            bool ok = zok;
+            const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
+            const int gx = wrap_or_flag(x0 - R + col, nx, periodic, ok);
+            slot_smem[row * PITCH + (A - R) + col] =
+                ok ? plane[(size_t)gy * nx + gx] : Storage<T>::from_float(0.0f);
+        }
+    }
+}
+
+// VX consecutive values of a global array as floats (vector load when allowed).
+template <typename T, int VX>
+__device__ __forceinline__ void load_cells(const T *__restrict__ src, bool vec, int nvalid,
+                                           float (&v)[VX]) {
+    if (vec) {
+        uint4 raw = __ldg(reinterpret_cast<const uint4 *>(src));
+        const T *e = reinterpret_cast<const T *>(&raw);
+#pragma unroll
+        for (int i = 0; i < VX; ++i) v[i] = Storage<T>::to_float(e[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < VX; ++i) v[i] = i < nvalid ? Storage<T>::to_float(src[i]) : 0.0f;
+    }
+}
+
+template <typename T, int VX>
+__device__ __forceinline__ void store_cells(T *dst, bool vec, int nvalid, const float (&v)[VX]) {
+    if (vec) {
+        T tmp[VX];
+#pragma unroll
+        for (int i = 0; i < VX; ++i) tmp[i] = Storage<T>::from_float(v[i]);
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tmp);
+    } else {
+#pragma unroll
+        for (int i = 0; i < VX; ++i)
+            if (i < nvalid) dst[i] = Storage<T>::from_float(v[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// General variable-coefficient sweep (forward or adjoint)
+// ---------------------------------------------------------------------------------------
+template <typename T, int NDIM, int SHAPE, int R, bool ADJ>
+__global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ VarParams<T> p) {
+    constexpr int VX = 16 / (int)sizeof(T), A = VX, TX = 128, BX = TX / VX;
+    constexpr int PITCH = TX + 2 * A;
+    constexpr int RZ = NDIM == 3 ? R : 0;
+    constexpr int NSLOT = 2 * RZ + 2;  // planes zo-RZ .. zo+RZ plus one in flight
+    using OT = OffsetTable<NDIM, SHAPE, R>;
+    static_assert(OT::count <= kMaxVarPts, "too many coefficient arrays");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    const int by = blockDim.y, tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * BX + tx, nthr = BX * by;
+    const int TY = by;  // one row per thread
+    const int rows = TY + 2 * R;
+    const int plane_elems = PITCH * rows;
+    int b = blockIdx.x;
+    const int tix = b % p.tiles_x;
+    b /= p.tiles_x;
+    const int tiy = b % p.tiles_y, tiz = b / p.tiles_y;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int x0 = tix * TX, y0 = tiy * TY;
+    const int z_begin = NDIM == 3 ? tiz * p.zchunk : 0;
+    const int z_end = NDIM == 3 ? min(nz, z_begin + p.zchunk) : 1;
+    const bool periodic = p.periodic != 0, aligned = p.aligned != 0;
+    const size_t pstride = (size_t)nx * ny;
+    const int ox = x0 + tx * VX, oy = y0 + ty;
+    const bool vec = aligned && ox + VX <= nx;
+    const int nvalid = nx - ox;
+
+    auto load = [&](int zi) {
+        const int slot = ((zi - z_begin + RZ) % NSLOT + NSLOT) % NSLOT;
+        load_tile_plane<T, R, A, PITCH>(p.in, smem + slot * plane_elems, zi, nx, ny, nz, periodic,
+                                        aligned, x0, y0, rows, tid, nthr, NDIM == 3);
+    };
+    // prologue: planes z_begin-RZ .. z_begin+RZ
+    for (int zi = z_begin - RZ; zi <= z_begin + RZ; ++zi) {
+        load(zi);
+        cp_async_commit();
+    }
+    for (int zo = z_begin; zo < z_end; ++zo) {
+        // plane zo+RZ+1 goes into the slot freed by plane zo-RZ-1
+        if (zo + RZ + 1 < z_end + RZ) load(zo + RZ + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        float acc[VX];
+#pragma unroll
+        for (int i = 0; i < VX; ++i) acc[i] = 0.0f;
+        const bool row_ok = oy < ny;
+        static_for<2 * RZ + 1>([&](auto dzi_c) {
+            constexpr int dz = decltype(dzi_c)::value - RZ;
+            // forward reads plane zo+dz at rows/cols +d; the adjoint reads plane zo-dz at -d
+            const int zsrc = ADJ ? zo - dz : zo + dz;
+            const int slot = ((zsrc - z_begin + RZ) % NSLOT + NSLOT) % NSLOT;
+            const T *sp = smem + slot * plane_elems;
+            static_for<2 * R + 1>([&](auto dyi_c) {
+                constexpr int dy = decltype(dyi_c)::value - R;
+                constexpr int m = OT::tab.mdx[dz + R][dy + R];
+                if constexpr (m >= 0) {
+                    constexpr int ry = ADJ ? -dy : dy;
+                    float win[VX + 2 * R];
+                    load_span<T, -m, VX + m, -R>(sp + (ty + R + ry) * PITCH + A + tx * VX, win);
+                    static_for<2 * R + 1>([&](auto dxi_c) {
+                        constexpr int dx = decltype(dxi_c)::value - R;
+                        constexpr int idx = OT::index(dz, dy, dx);
+                        if constexpr (idx >= 0) {
+                            constexpr int rx = ADJ ? -dx : dx;
+                            float w[VX];
+                            if (!row_ok) {
+#pragma unroll
+                                for (int i = 0; i < VX; ++i) w[i] = 0.0f;
+                            } else if constexpr (!ADJ) {
+                                load_cells<T, VX>(p.w[idx] + (size_t)zo * pstride +
+                                                      (size_t)oy * nx + ox,
+                                                  vec, nvalid, w);
+                            } else {
+                                // coefficient at the source cell q - o (wrapped; a source
+                                // outside a Dirichlet grid reads 0 from the tile anyway)
+                                bool ok = true;
+                                const int gz = NDIM == 3 ? wrap_or_flag(zo - dz, nz, true, ok) : 0;
+                                const int gy = wrap_or_flag(oy - dy, ny, true, ok);
+                                const T *base = p.w[idx] + (size_t)gz * pstride + (size_t)gy * nx;
+#pragma unroll
+                                for (int i = 0; i < VX; ++i) {
+                                    bool okx = true;
+                                    const int gx = wrap_or_flag(ox + i - dx, nx, true, okx);
+                                    w[i] = Storage<T>::to_float(__ldg(base + gx));
+                                }
+                            }
+#pragma unroll
+                            for (int i = 0; i < VX; ++i)
+                                acc[i] = fmaf(w[i], win[i + rx + R], acc[i]);
+                        }
+                    });
+                }
+            });
+        });
+        if (row_ok && ox < nx)
+            store_cells<T, VX>(p.out + (size_t)zo * pstride + (size_t)oy * nx + ox, vec, nvalid,
+                               acc);
+        __syncthreads();  // the slot of plane zo-RZ is refilled next iteration
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------------
+// div(k grad u)
+// ---------------------------------------------------------------------------------------
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) divkgrad_kernel(const __grid_constant__ VarParams<T> p) {
+    constexpr int VX = 16 / (int)sizeof(T), A = VX, TX = 128, BX = TX / VX, R = 1;
+    constexpr int PITCH = TX + 2 * A;
+    constexpr int RZ = NDIM == 3 ? 1 : 0;
+    constexpr int NSLOT = 2 * RZ + 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *su = reinterpret_cast<T *>(smem_raw);
+    const int by = blockDim.y, tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * BX + tx, nthr = BX * by;
+    const int TY = by;
+    const int rows = TY + 2 * R;
+    const int plane_elems = PITCH * rows;
+    T *sk = su + NSLOT * plane_elems;
+    int b = blockIdx.x;
+    const int tix = b % p.tiles_x;
+    b /= p.tiles_x;
+    const int tiy = b % p.tiles_y, tiz = b / p.tiles_y;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int x0 = tix * TX, y0 = tiy * TY;
+    const int z_begin = NDIM == 3 ? tiz * p.zchunk : 0;
+    const int z_end = NDIM == 3 ? min(nz, z_begin + p.zchunk) : 1;
+    const bool periodic = p.periodic != 0, aligned = p.aligned != 0;
+    const size_t pstride = (size_t)nx * ny;
+    const int ox = x0 + tx * VX, oy = y0 + ty;
+    const bool vec = aligned && ox + VX <= nx;
+    const int nvalid = nx - ox;
+    const T *kfield = p.w[0];
+
+    auto slot_of = [&](int zi) { return ((zi - z_begin + RZ) % NSLOT + NSLOT) % NSLOT; };
+    auto load = [&](int zi) {
+        const int s = slot_of(zi);
+        load_tile_plane<T, R, A, PITCH>(p.in, su + s * plane_elems, zi, nx, ny, nz, periodic,
+                                        aligned, x0, y0, rows, tid, nthr, NDIM == 3);
+        load_tile_plane<T, R, A, PITCH>(kfield, sk + s * plane_elems, zi, nx, ny, nz, periodic,
+                                        aligned, x0, y0, rows, tid, nthr, NDIM == 3);
+    };
+    for (int zi = z_begin - RZ; zi <= z_begin + RZ; ++zi) {
+        load(zi);
+        cp_async_commit();
+    }
+    const int off = (ty + R) * PITCH + A + tx * VX;  // the thread's first cell in a slot
+    for (int zo = z_begin; zo < z_end; ++zo) {
+        if (zo + RZ + 1 < z_end + RZ) load(zo + RZ + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        if (oy < ny && ox < nx) {
+            const int s0 = slot_of(zo) * plane_elems + off;
+            float u0[VX + 2], k0[VX + 2];  // centre row with one cell each side
+            load_span<T, -1, VX + 1, -1>(su + s0, u0);
+            load_span<T, -1, VX + 1, -1>(sk + s0, k0);
+            float acc[VX];
+#pragma unroll
+            for (int i = 0; i < VX; ++i) acc[i] = 0.0f;
+            // a neighbour outside a Dirichlet grid has u = 0 and k = k[p]
+            auto face = [&](int i, float un, float kn, bool inside) {
+                const float kc = k0[i + 1];
+                const float kf = inside ? 0.5f * (kc + kn) : kc;
+                const float du = (inside ? un : 0.0f) - u0[i + 1];
+                acc[i] = fmaf(kf, du, acc[i]);
+            };
+            // axes in the oracle's order: z, y, x; within an axis the + face then the - face
+            if constexpr (NDIM == 3) {
+                const int sp = slot_of(zo + 1) * plane_elems + off;
+                const int sm = slot_of(zo - 1) * plane_elems + off;
+                float up[VX], kp[VX], um[VX], km[VX];
+                load_span<T, 0, VX, 0>(su + sp, up);
+                load_span<T, 0, VX, 0>(sk + sp, kp);
+                load_span<T, 0, VX, 0>(su + sm, um);
+                load_span<T, 0, VX, 0>(sk + sm, km);
+                const bool inp = periodic || zo + 1 < nz, inm = periodic || zo - 1 >= 0;
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    face(i, up[i], kp[i], inp);
+                    face(i, um[i], km[i], inm);
+                }
+            }
+            {
+                float up[VX], kp[VX], um[VX], km[VX];
+                load_span<T, 0, VX, 0>(su + off + slot_of(zo) * plane_elems + PITCH, up);
+                load_span<T, 0, VX, 0>(sk + off + slot_of(zo) * plane_elems + PITCH, kp);
+                load_span<T, 0, VX, 0>(su + off + slot_of(zo) * plane_elems - PITCH, um);
+                load_span<T, 0, VX, 0>(sk + off + slot_of(zo) * plane_elems - PITCH, km);
+                const bool inp = periodic || oy + 1 < ny, inm = periodic || oy - 1 >= 0;
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    face(i, up[i], kp[i], inp);
+                    face(i, um[i], km[i], inm);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < VX; ++i) {
+                const bool inp = periodic || ox + i + 1 < nx, inm = periodic || ox + i - 1 >= 0;
+                face(i, u0[i + 2], k0[i + 2], inp);
+                face(i, u0[i], k0[i], inm);
+            }
+            store_cells<T, VX>(p.out + (size_t)zo * pstride + (size_t)oy * nx + ox, vec, nvalid,
+                               acc);
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace gst

@@ -1,0 +1,119 @@
+// Host-side launchers of the variable-coefficient and div(k grad u) kernels.
+#pragma once
+
+#include "internal.h"
+#include "var.cuh"
+
+namespace gst {
+
+// Offset sets with at most kMaxVarPts points have VAR kernels.
+constexpr bool var_compiled(int ndim, int shape, int r) {
+    return r >= 1 && r <= 4 && shape_count(ndim, shape, r) <= kMaxVarPts;
+}
+
+template <typename T> static int fill_var_params(const VarLaunch &L, VarParams<T> &p, int by) {
+    constexpr int VX = 16 / (int)sizeof(T), TX = 128;
+    p.in = static_cast<const T *>(L.in);
+    p.out = static_cast<T *>(L.out);
+    bool ptr_ok = ((uintptr_t)L.in % 16 == 0) && ((uintptr_t)L.out % 16 == 0);
+    for (int i = 0; i < kMaxVarPts; ++i) p.w[i] = nullptr;
+    for (int i = 0; i < L.narrays; ++i) {
+        p.w[i] = static_cast<const T *>(L.arrays[i]);
+        if ((uintptr_t)L.arrays[i] % 16) ptr_ok = false;
+    }
+    p.nx = (int)L.nx;
+    p.ny = (int)L.ny;
+    p.nz = L.ndim == 3 ? (int)L.nz : 1;
+    p.periodic = L.periodic;
+    p.aligned = (ptr_ok && (L.nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
+    p.tiles_x = (int)((L.nx + TX - 1) / TX);
+    p.tiles_y = (int)((L.ny + by - 1) / by);
+    p.zchunk = (L.ndim == 3 && L.z_chunk > 0) ? L.z_chunk : p.nz;
+    (void)VX;
+    return 0;
+}
+
+template <typename T, int NDIM, int SHAPE, int R, bool ADJ>
+int launch_var_t(const VarLaunch &L) {
+    constexpr int VX = 16 / (int)sizeof(T), BX = 128 / VX, PITCH = 128 + 2 * VX;
+    constexpr int RZ = NDIM == 3 ? R : 0;
+    constexpr int NSLOT = 2 * RZ + 2;
+    const int by = L.block_y > 0 ? L.block_y : 8;
+    if (BX * by > 256 || (BX * by) % 32) return -1;
+    VarParams<T> p;
+    fill_var_params<T>(L, p, by);
+    const int64_t zchunks = NDIM == 3 ? (p.nz + p.zchunk - 1) / p.zchunk : 1;
+    const int64_t nblocks = (int64_t)p.tiles_x * p.tiles_y * zchunks;
+    if (nblocks > INT32_MAX) return -2;
+    const size_t smem = (size_t)NSLOT * PITCH * (by + 2 * R) * sizeof(T);
+    auto kern = var_sweep_kernel<T, NDIM, SHAPE, R, ADJ>;
+    static size_t smem_set = 0;
+    if (smem > 48 * 1024 && smem > smem_set) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -4;
+        smem_set = smem;
+    }
+    kern<<<(unsigned)nblocks, dim3(BX, by), smem, L.stream>>>(p);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <typename T, int NDIM, bool ADJ> int launch_var_shape(const VarLaunch &L) {
+#define GST_VAR(S, RR)                                                      \
+    if (L.shape == S && L.radius == RR) {                                   \
+        if constexpr (var_compiled(NDIM, S, RR))                            \
+            return launch_var_t<T, NDIM, S, RR, ADJ>(L);                    \
+        else                                                                \
+            return -2;                                                      \
+    }
+    GST_VAR(kStar, 1) GST_VAR(kStar, 2) GST_VAR(kStar, 3) GST_VAR(kStar, 4)
+    GST_VAR(kBox, 1) GST_VAR(kBox, 2) GST_VAR(kBox, 3) GST_VAR(kBox, 4)
+    GST_VAR(kDiamond, 1) GST_VAR(kDiamond, 2) GST_VAR(kDiamond, 3) GST_VAR(kDiamond, 4)
+#undef GST_VAR
+    return -2;
+}
+
+template <typename T, bool ADJ> int launch_var_dt(const VarLaunch &L) {
+    if (L.ndim == 2) return launch_var_shape<T, 2, ADJ>(L);
+    if (L.ndim == 3) return launch_var_shape<T, 3, ADJ>(L);
+    return -1;
+}
+
+template <typename T> int launch_divkgrad_t(const VarLaunch &L) {
+    constexpr int VX = 16 / (int)sizeof(T), BX = 128 / VX, PITCH = 128 + 2 * VX;
+    const int by = L.block_y > 0 ? L.block_y : 8;
+    if (BX * by > 256 || (BX * by) % 32) return -1;
+    VarParams<T> p;
+    fill_var_params<T>(L, p, by);
+    const int nslot = L.ndim == 3 ? 4 : 2;
+    const int64_t zchunks = L.ndim == 3 ? (p.nz + p.zchunk - 1) / p.zchunk : 1;
+    const int64_t nblocks = (int64_t)p.tiles_x * p.tiles_y * zchunks;
+    if (nblocks > INT32_MAX) return -2;
+    const size_t smem = 2 * (size_t)nslot * PITCH * (by + 2) * sizeof(T);
+    if (L.ndim == 3) {
+        auto kern = divkgrad_kernel<T, 3>;
+        static size_t set3 = 0;
+        if (smem > 48 * 1024 && smem > set3) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return -4;
+            set3 = smem;
+        }
+        kern<<<(unsigned)nblocks, dim3(BX, by), smem, L.stream>>>(p);
+    } else {
+        auto kern = divkgrad_kernel<T, 2>;
+        static size_t set2 = 0;
+        if (smem > 48 * 1024 && smem > set2) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return -4;
+            set2 = smem;
+        }
+        kern<<<(unsigned)nblocks, dim3(BX, by), smem, L.stream>>>(p);
+    }
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+}  // namespace gst

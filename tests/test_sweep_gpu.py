@@ -84,7 +84,7 @@ def test_scalar_loader_odd_row_length(ndim, shape, bc):
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("vec_y", [1, 2])
-@pytest.mark.parametrize("blocks", [(32, 8), (32, 4), (16, 8), (64, 2)])
+@pytest.mark.parametrize("blocks", [(32, 8), (32, 4), (32, 2), (32, 1)])
 def test_stream_variants_agree(shape, vec_y, blocks):
     r = 1
     dims = (19, 45, 200)
