@@ -149,7 +149,8 @@ typedef struct {
 } stencil_batch_item;
 
 /* stencil_batch_plan -- build a tile work list over `n` grids (2D, constant coefficients,
- * any mix of shapes, radii <= 4, dtypes and sizes) for `steps` sweeps each, allocate the
+ * any mix of star/box/diamond shapes of radius 1-2, dtypes, boundaries and sizes; other
+ * plans give UNSUPPORTED) for `steps` sweeps each, allocate the
  * device scratch it needs, and capture one persistent cooperative kernel (plus the reset of
  * its counters) into a CUDA graph.  Every step boundary is a device-wide barrier whose wait
  * is bounded; an expired wait latches STENCIL_ERR_TIMEOUT.  The plans and buffers named by
@@ -164,6 +165,17 @@ int stencil_batch_status(stencil_batch b, void *stream);
 
 /* stencil_batch_destroy -- free the batch, its graph and its scratch. */
 int stencil_batch_destroy(stencil_batch b);
+
+/* stencil_batch_set_wait_limit -- set the bound on every device-side barrier wait of the
+ * batch (default 2 s) and, for fault-injection tests only, a number of extra arrivals each
+ * barrier waits for that never come (0 in normal use).  With phantom_arrivals > 0 a launch of
+ * more than one step ends with STENCIL_ERR_TIMEOUT after about `seconds`, without hanging.
+ * Synchronises the device. */
+int stencil_batch_set_wait_limit(stencil_batch b, double seconds, int phantom_arrivals);
+
+/* stencil_batch_info -- work tiles, persistent blocks and whether the launch was captured in
+ * a CUDA graph (1) or is issued directly (0).  Any pointer may be NULL. */
+int stencil_batch_info(stencil_batch b, int *ntiles, int *nblocks, int *graph_captured);
 
 /* ---- tuning and dispatch ----------------------------------------------------------------- */
 

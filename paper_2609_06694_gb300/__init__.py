@@ -8,6 +8,7 @@ library raises instead of falling back to anything else.
 from .api import (  # noqa: F401
     FAMILY_FUSED2D,
     FAMILY_STREAM,
+    Batch,
     Plan,
     StencilError,
     library_path,
@@ -17,6 +18,11 @@ from .api import (  # noqa: F401
     stencil_apply_adjoint_var,
     stencil_apply_host,
     stencil_apply_var,
+    stencil_batch_info,
+    stencil_batch_launch,
+    stencil_batch_plan,
+    stencil_batch_set_wait_limit,
+    stencil_batch_status,
     stencil_launch_count,
     stencil_load_dispatch_map,
     stencil_offsets,

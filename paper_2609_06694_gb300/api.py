@@ -75,6 +75,8 @@ def _lib():
         "stencil_batch_launch": ([P, P], I),
         "stencil_batch_status": ([P, P], I),
         "stencil_batch_destroy": ([P], I),
+        "stencil_batch_set_wait_limit": ([P, ctypes.c_double, I], I),
+        "stencil_batch_info": ([P, P, P, P], I),
         "stencil_plan_get_variant": ([P, ctypes.POINTER(stencil_variant)], I),
         "stencil_plan_set_variant": ([P, ctypes.POINTER(stencil_variant)], I),
         "stencil_load_dispatch_map": ([ctypes.c_char_p], I),
@@ -264,3 +266,53 @@ def stencil_strerror(code: int) -> str:
 
 def stencil_abi_version() -> int:
     return _lib().stencil_abi_version()
+
+
+class Batch:
+    """Owns a ``stencil_batch``; keeps the plans and tensors it references alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _LIB is not None:
+            _LIB.stencil_batch_destroy(h)
+            self.handle = None
+
+
+def stencil_batch_plan(items, steps) -> Batch:
+    """items: sequence of (Plan, in_tensor, out_tensor); all 2D const plans."""
+    lib = _lib()
+    arr = (stencil_batch_item * len(items))()
+    for i, (plan, inp, out) in enumerate(items):
+        plan._check_tensor(inp, f"items[{i}].in")
+        plan._check_tensor(out, f"items[{i}].out")
+        arr[i].plan = plan.handle.value
+        arr[i].in_ = inp.data_ptr()
+        arr[i].out = out.data_ptr()
+    h = ctypes.c_void_p()
+    _check(lib.stencil_batch_plan(ctypes.byref(h), arr, len(items), int(steps)),
+           "stencil_batch_plan")
+    return Batch(h.value, list(items))
+
+
+def stencil_batch_launch(batch: Batch, stream=None):
+    _check(_lib().stencil_batch_launch(batch.handle, _stream_ptr(stream)), "stencil_batch_launch")
+
+
+def stencil_batch_status(batch: Batch, stream=None) -> int:
+    return _lib().stencil_batch_status(batch.handle, _stream_ptr(stream))
+
+
+def stencil_batch_set_wait_limit(batch: Batch, seconds: float, phantom_arrivals: int = 0):
+    _check(_lib().stencil_batch_set_wait_limit(batch.handle, float(seconds),
+                                               int(phantom_arrivals)), "set_wait_limit")
+
+
+def stencil_batch_info(batch: Batch) -> dict:
+    nt, nb, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib().stencil_batch_info(batch.handle, ctypes.byref(nt), ctypes.byref(nb),
+                                     ctypes.byref(g)), "stencil_batch_info")
+    return {"tiles": nt.value, "blocks": nb.value, "graph": bool(g.value)}

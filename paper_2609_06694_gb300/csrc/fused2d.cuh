@@ -24,10 +24,27 @@ struct Fused2DTile {
     int steps;        // steps fused (>= 1)
 };
 
+// A load that bypasses L1 (cache at L2 only): needed when other SMs wrote the buffer earlier
+// in the same launch and this SM may still hold stale lines of it.
+template <typename T> __device__ __forceinline__ T load_l2(const T *p) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 2, "4- or 2-byte values");
+    if constexpr (sizeof(T) == 4) {
+        unsigned int v = __ldcg(reinterpret_cast<const unsigned int *>(p));
+        T r;
+        memcpy(&r, &v, 4);
+        return r;
+    } else {
+        unsigned short v = __ldcg(reinterpret_cast<const unsigned short *>(p));
+        T r;
+        memcpy(&r, &v, 2);
+        return r;
+    }
+}
+
 // Runs `t.steps` sweeps on one tile.  `buf` holds 2 * (th + 2H) * (tw + 2H) floats.
 // `coef(idx)` returns the coefficient of canonical offset idx.  All threads of the block must
-// call this; it ends with a __syncthreads().
-template <typename T, int SHAPE, int R, typename Coef>
+// call this; it ends with a __syncthreads().  COHERENT loads the input through L2 only.
+template <typename T, int SHAPE, int R, bool COHERENT = false, typename Coef>
 __device__ __forceinline__ void fused2d_tile(const T *__restrict__ in, T *__restrict__ out,
                                              const Fused2DTile &t, float *buf, const Coef &coef) {
     const int H = R * t.steps;
@@ -45,7 +62,8 @@ __device__ __forceinline__ void fused2d_tile(const T *__restrict__ in, T *__rest
         bool ok = true;
         int gy = wrap_or_flag(t.y0 - H + row, t.ny, periodic, ok);
         int gx = wrap_or_flag(t.x0 - H + col, t.nx, periodic, ok);
-        src[e] = ok ? Storage<T>::to_float(in[(size_t)gy * t.nx + gx]) : 0.0f;
+        const T *a = in + (size_t)gy * t.nx + gx;
+        src[e] = ok ? Storage<T>::to_float(COHERENT ? load_l2(a) : *a) : 0.0f;
     }
     __syncthreads();
 
