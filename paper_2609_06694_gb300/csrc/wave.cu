@@ -267,8 +267,10 @@ static int wave_step(wave_plan_s *p, bool adj, const float *u, const float *upre
     const unsigned nblocks = (unsigned)(q.tiles_x * q.tiles_y * zchunks);
     const int R = p->radius;
     const size_t smem = (size_t)(2 * R + 2) * (128 + 8) * (by + 2 * R) * sizeof(float);
+    // shared-memory opt-in already granted, per (radius, direction) kernel
+    static size_t smem_set[5][2] = {};
+    size_t &set = smem_set[R][adj ? 1 : 0];
     auto go = [&](auto kern) -> int {
-        static size_t set = 0;  // one per kernel instantiation
         if (smem > set) {
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem) != cudaSuccess)

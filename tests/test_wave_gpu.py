@@ -172,18 +172,25 @@ def test_full_size_gradient_properties():
     g50 = torch.empty_like(g)
     W.wave_gradient(plan50, v32, obs, tr, J50, g50)
     assert J50.item() == J.item() and torch.equal(g50, g)
-    # finite-difference directional derivative along a smooth bump at the perturbation
+    # Finite-difference directional derivative.  The receivers (z = 10) do not see the
+    # centre of the grid within 500 steps, so the direction is a smooth bump the recorded
+    # wavefield crosses (between source and receivers), and the observed record is zero so
+    # that J is far above the f32 rounding of the traces.
+    zero = torch.zeros_like(obs)
+    g0 = torch.empty_like(g)
+    J0 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    W.wave_gradient(plan25, v32, zero, tr, J0, g0)
     zz, yy, xx = np.meshgrid(*[np.arange(256.0)] * 3, indexing="ij")
-    e = np.exp(-((zz - 128) ** 2 + (yy - 128) ** 2 + (xx - 128) ** 2) / (2 * 20.0 ** 2))
-    eps = 2.0  # m/s
+    e = np.exp(-((zz - 24) ** 2 + (yy - 128) ** 2 + (xx - 150) ** 2) / (2 * 12.0 ** 2))
+    eps = 4.0  # m/s
     Js = []
     for sgn in (1, -1):
         trs = torch.empty_like(tr)
         W.wave_forward(plan25, f32dev(P["v"] + sgn * eps * e), trs)
         Jx = torch.zeros(1, dtype=torch.float64, device="cuda")
-        W.wave_misfit(plan25, trs, obs, Jx)
+        W.wave_misfit(plan25, trs, zero, Jx)
         Js.append(Jx.item())
     fd = (Js[0] - Js[1]) / (2 * eps)
-    ad = float((g * torch.from_numpy(e).cuda()).sum())
+    ad = float((g0 * torch.from_numpy(e).cuda()).sum())
     print(f"256^3 x 500: J={J.item():.6e}  <g,e>={ad:.6e}  FD={fd:.6e}  rel={abs(fd-ad)/abs(ad):.2e}")
     assert abs(fd - ad) <= 1e-2 * abs(ad)
