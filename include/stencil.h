@@ -136,6 +136,25 @@ int stencil_apply_adjoint_var(stencil_handle h, const void *in,
 int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, int steps,
                        void *stream);
 
+/* stencil_apply_noalloc -- stencil_apply for callers that may not allocate device memory.
+ * The paper has no counterpart; this is a library service.  stencil_apply obtains its
+ * multi-step scratch grid with cudaMalloc on first use, which some callers cannot allow: code
+ * inside a framework whose memory pool already holds the device's memory, latency-critical
+ * loops that cannot absorb cudaMalloc's implicit device synchronisation, and work issued while
+ * a stream is being captured.  This call computes the same sweeps (same kernels, same step
+ * grouping, same results) but ping-pongs through a fixed array compiled into the library:
+ *   - no cudaMalloc/cudaFree or other allocating call is made;
+ *   - grids larger than STENCIL_NOALLOC_SCRATCH_BYTES (in bytes of the storage type) are
+ *     rejected with STENCIL_ERR_BADARG before anything is launched;
+ *   - the array is reserved on every GPU that loads the library, until the process exits;
+ *   - the first call on each device looks up the array's device address with that device
+ *     current; make that first call before any stream capture begins;
+ *   - all calls share the array, so calls whose kernels may run at the same time on the GPU
+ *     (different streams, no ordering) race and must be serialised by the caller.
+ * Arguments, plan kinds and errors otherwise as stencil_apply. */
+#define STENCIL_NOALLOC_SCRATCH_BYTES ((size_t)16 * 1024 * 1024)
+int stencil_apply_noalloc(stencil_handle h, const void *in, void *out, int steps, void *stream);
+
 /* stencil_sync_status -- synchronise `stream` and return the first error latched by a kernel
  * of this plan since the last call (then clear it). */
 int stencil_sync_status(stencil_handle h, void *stream);

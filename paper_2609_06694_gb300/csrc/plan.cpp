@@ -560,3 +560,14 @@ int stencil_apply_adjoint_var(stencil_handle h, const void *in, const void *cons
 }
 
 }  // extern "C"
+
+namespace gst {
+
+// One launch of `k` steps with an explicit destination (used by the allocation-free entry
+// point, which supplies its own ping-pong buffer).
+int launch_group_with(stencil_plan_s &p, const float *cf, const void *src, void *dst, int k,
+                      cudaStream_t s) {
+    return launch_group(p, cf, src, dst, k, s);
+}
+
+}  // namespace gst

@@ -35,5 +35,7 @@ int run_steps(stencil_plan_s &p, const float *cf, const void *in, void *out, int
               cudaStream_t s);
 int check_apply_args(const stencil_plan_s *p, const void *in, const void *out, int steps);
 bool overlaps(const void *a, const void *b, size_t n);
+int launch_group_with(stencil_plan_s &p, const float *cf, const void *src, void *dst, int k,
+                      cudaStream_t s);
 int map_launch_rc(int rc);
 }  // namespace gst
