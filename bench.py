@@ -160,7 +160,7 @@ def traffic_from_profile(kernel_tag):
             if ln.startswith("- ") and ":" in ln:
                 k, v = ln[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-        if vals.get("stream.cuh sha256[:16]") != sha:
+        if vals.get("stream.cuh sha256 prefix") != sha:
             return None
         return float(vals["dram bytes per launch"])
     except Exception:

@@ -221,7 +221,8 @@ int stencil_plan_set_variant(stencil_handle h, const stencil_variant *v);
 /* stencil_load_dispatch_map -- replace the process-wide dispatch map with the one in the
  * text file at `path` (format: lines "ndim shape radius dtype boundary kind size_class :
  * family block_x block_y vec_y z_chunk fuse tile_x tile_y", '#' comments).  Plans created
- * afterwards use it.  NULL restores the built-in defaults. */
+ * afterwards use it.  NULL restores the built-in defaults.  If the environment variable
+ * STENCIL_DISPATCH_MAP names a file, it is loaded once before the first stencil_plan. */
 int stencil_load_dispatch_map(const char *path);
 
 /* stencil_size_class -- the size class (0 .. 3) a grid of `cells` cells falls in. */

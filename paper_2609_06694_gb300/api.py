@@ -45,6 +45,7 @@ class stencil_batch_item(ctypes.Structure):
 
 
 _LIB = None
+DISPATCH_MAP = os.path.join(os.path.dirname(os.path.abspath(__file__)), "dispatch_map.txt")
 
 
 def library_path() -> str:
@@ -91,6 +92,9 @@ def _lib():
             fn.argtypes = args
             fn.restype = res
     _LIB = lib
+    # the dispatch map written by the autotuner ships with the package
+    if os.path.exists(DISPATCH_MAP):
+        lib.stencil_load_dispatch_map(DISPATCH_MAP.encode())
     return lib
 
 

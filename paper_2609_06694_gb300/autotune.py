@@ -40,7 +40,7 @@ def stream_candidates(ndim, shape, radius, dtype, quick=False):
     if radius == 1:
         vys.append(4)
     bys = [b for b in (1, 2, 4, 8, 16) if 32 <= bx * b <= 256 and (bx * b) % 32 == 0]
-    zcs = [0] if ndim == 2 else ([64, 128] if quick else [32, 64, 128, 256])
+    zcs = [0] if ndim == 2 else ([0, 64] if quick else [0, 32, 64, 128])
     for vy, by, zc in itertools.product(vys, bys, zcs):
         out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=vy, z_chunk=zc,
                         fuse=1, tile_x=0, tile_y=0))

@@ -17,11 +17,17 @@ struct StreamLaunch {
     const void *in;
     void *out;
     int block_x, block_y, vec_y, z_chunk;
+    int use_tma = 1;         // 0 forces the cp.async loader (tensor maps are used when legal)
     int *err;                // device error word or null
     cudaStream_t stream;
 };
 
 // Returns 0, or a negative STENCIL_ERR_* code.  One per storage type and dimension.
+// Largest CTA of a streaming kernel (kept in step with StreamKernel::MAX_THREADS).
+constexpr int stream_max_threads(int ndim, int shape, int radius, int vec_y) {
+    return (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 1) ? 512 : 256;
+}
+
 // Defined in stream_<dtype>_<ndim>d_<shape>.cu.
 #define GST_DECLARE_STREAM(DT, ND)                          \
     int launch_stream_##DT##_##ND##d_star(const StreamLaunch &L); \

@@ -74,7 +74,7 @@ static stencil_variant default_variant(const stencil_plan_s &p) {
     v.block_x = 128 / vx;  // 128-cell tiles in x
     v.block_y = 256 / v.block_x;
     v.vec_y = 1;
-    v.z_chunk = p.ndim == 3 ? 128 : 0;
+    v.z_chunk = 0;  // balanced persistent split
     v.fuse = 1;
     if (p.ndim == 3) {
         // two rows per thread while the partial-sum queue stays small
@@ -119,7 +119,8 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
     if (v.family == STENCIL_FAMILY_STREAM) {
         // tiles are 128 cells wide: one 16-byte vector of cells per thread along x
         if (v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
-            v.block_x * v.block_y > 256 || (v.block_x * v.block_y) % 32 != 0)
+            v.block_x * v.block_y > stream_max_threads(p.ndim, p.shape, p.radius, v.vec_y) ||
+            (v.block_x * v.block_y) % 32 != 0)
             return STENCIL_ERR_BADARG;
         if (!stream_vy_compiled(p.ndim, p.shape, p.radius, v.vec_y))
             return STENCIL_ERR_UNSUPPORTED;
@@ -271,6 +272,12 @@ const char *stencil_strerror(int code) {
 
 int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, int radius,
                  int kind, const double *coeffs, int64_t ncoeffs, int dtype, int boundary) {
+    // a dispatch map named by STENCIL_DISPATCH_MAP is read once, before the first plan
+    static std::once_flag env_map_once;
+    std::call_once(env_map_once, [] {
+        const char *path = std::getenv("STENCIL_DISPATCH_MAP");
+        if (path && *path) stencil_load_dispatch_map(path);
+    });
     if (!out) return STENCIL_ERR_BADARG;
     *out = nullptr;
     if ((ndim != 2 && ndim != 3) || !dims) return STENCIL_ERR_BADARG;
