@@ -327,7 +327,7 @@ def _oracle_sample(seed_star=2001, seed_box=2003, nz=16):
 
 
 def cpu_baseline_sample(W=None):
-    updates, dt, desc = _oracle_sample(nz=96)
+    updates, dt, desc = _oracle_sample(nz=256)
     return {"value": round(updates / dt / 1e9, 6), "unit": "Gcell-updates/s", "cores": 1,
             "kind": "oracle", "sample": desc, "seconds": round(dt, 2)}
 
@@ -362,6 +362,148 @@ def bench_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------
+# --suite: the other workloads, one JSON line each (reported next to the bench line; not bench
+# lines themselves).  Times are CUDA-event medians over `reps` runs after warm-up.
+# ------------------------------------------------------------------------------------------
+def _time(fn, reps=5, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    return float(np.median(ts))
+
+
+def suite():
+    import torch
+
+    from paper_2609_06694_gb300 import build
+    build.build()
+    import paper_2609_06694_gb300 as gs
+    from paper_2609_06694_gb300 import inputs
+    from paper_2609_06694_gb300 import wave as W
+
+    torch.cuda.set_device(0)
+    peak, _ = measured_peaks()
+    out = []
+
+    # 2D 5-point Jacobi 512^2, 10 steps (L2-resident: latency-bound, reported formally vs HBM)
+    dims = (512, 512)
+    plan = gs.stencil_plan(2, dims, "star", 1, "const", np.full(5, 0.2), "f32", "dirichlet")
+    x = inputs.to_storage(inputs.uniform(1001, dims), "f32").cuda()
+    y = torch.empty_like(x)
+    ms = _time(lambda: gs.stencil_apply(plan, x, y, 10), reps=20)
+    out.append({"workload": "2D Jacobi 512^2 f32 Dirichlet, 10 steps", "ms": round(ms, 4),
+                "Gcell_updates_per_s": round(512 * 512 * 10 / ms / 1e6, 2),
+                "variant": gs.stencil_plan_get_variant(plan),
+                "note": "1 MiB grid stays in L2: latency-bound, not HBM-bound"})
+
+    # 3D 512^3 single and 8-step sweeps (the bench workload, per part)
+    W3 = build_workload(torch.device("cuda", 0))
+    for name, xin in (("star", "x_star"), ("box", "x_box")):
+        for steps in (1, 8):
+            ms = _time(lambda: gs.stencil_apply(W3[name], W3[xin], W3["y"], steps))
+            gbs = 8 * CELLS * steps / (ms * 1e-3) / 1e9
+            out.append({"workload": f"3D 512^3 f32 periodic {'25-pt star r4' if name == 'star' else '27-pt box'}, {steps} step(s)",
+                        "ms": round(ms, 4), "Gcell_updates_per_s": round(CELLS * steps / ms / 1e6, 2),
+                        "alg_GBps": round(gbs, 1), "frac_measured_hbm": round(gbs / peak, 4),
+                        "frac_nominal_8TBps": round(gbs / 8000.0, 4)})
+    del W3
+    torch.cuda.empty_cache()
+
+    # div(k grad u) 384^3 in three storage types
+    n = 384
+    kk = inputs.lognormal_k(3002, (n, n, n))
+    uu = inputs.uniform(3001, (n, n, n))
+    for dt in ("f32", "f16", "bf16"):
+        plan = gs.stencil_plan(3, (n, n, n), "star", 1, "divkgrad", None, dt, "dirichlet")
+        k = inputs.to_storage(kk, dt).cuda()
+        u = inputs.to_storage(uu, dt).cuda()
+        y = torch.empty_like(u)
+        ms = _time(lambda: gs.stencil_apply_var(plan, u, [k], y, 1))
+        es = 4 if dt == "f32" else 2
+        gbs = 3 * es * n ** 3 / (ms * 1e-3) / 1e9
+        out.append({"workload": f"div(k grad u) 384^3 {dt} Dirichlet, 1 step", "ms": round(ms, 4),
+                    "Gcell_updates_per_s": round(n ** 3 / ms / 1e6, 2), "alg_GBps": round(gbs, 1),
+                    "frac_measured_hbm": round(gbs / peak, 4)})
+        del k, u, y
+    torch.cuda.empty_cache()
+
+    # batched 2D: 256 grids, 20 steps, one persistent launch vs plain per-grid sweeps
+    specs = inputs.batched_grid_specs()
+    for dt in ("f32", "bf16"):
+        items, plans = [], []
+        cells = 0
+        for i, sp in enumerate(specs):
+            d = (sp["ny"], sp["nx"])
+            npts = {"star": 4 * sp["radius"] + 1, "box": (2 * sp["radius"] + 1) ** 2}[sp["shape"]]
+            c = inputs.normalised_abs_weights(sp["weight_seed"], npts)
+            pl = gs.stencil_plan(2, d, sp["shape"], sp["radius"], "const", c, dt, "dirichlet")
+            xi = inputs.to_storage(inputs.uniform(sp["input_seed"], d), dt).cuda()
+            items.append((pl, xi, torch.empty_like(xi)))
+            cells += d[0] * d[1]
+        batch = gs.stencil_batch_plan(items, 20)
+        ms_b = _time(lambda: gs.stencil_batch_launch(batch), reps=5)
+
+        def plain_single_steps():
+            for pl, xi, yi in items:
+                gs.stencil_apply(pl, xi, yi, 1)
+
+        ms_1 = _time(plain_single_steps, reps=3, warm=1) * 20  # 256 x 20 single-step launches
+        ms_20 = _time(lambda: [gs.stencil_apply(pl, xi, yi, 20) for pl, xi, yi in items], reps=3,
+                      warm=1)
+        es = 4 if dt == "f32" else 2
+        gbs = 2 * es * cells * 20 / (ms_b * 1e-3) / 1e9
+        info = gs.stencil_batch_info(batch)
+        out.append({"workload": f"batched 2D, 256 grids, 20 steps, {dt}", "cells_per_step": cells,
+                    "ms_batched": round(ms_b, 3), "ms_plain_256x20_launches": round(ms_1, 3),
+                    "ms_plain_256_calls_of_20_steps": round(ms_20, 3),
+                    "speedup_vs_256x20": round(ms_1 / ms_b, 2),
+                    "speedup_vs_256_calls": round(ms_20 / ms_b, 2),
+                    "Gcell_updates_per_s": round(cells * 20 / ms_b / 1e6, 2),
+                    "alg_GBps": round(gbs, 1), "frac_measured_hbm": round(gbs / peak, 4),
+                    "batch": info})
+        del batch, items
+    torch.cuda.empty_cache()
+
+    # wave equation 256^3 x 500: forward, and gradient (forward + recompute + adjoint)
+    n3 = (256, 256, 256)
+    lap_plan = gs.stencil_plan(3, n3, "star", 4, "const", np.ones(25), "f32", "dirichlet")
+    lap = inputs.laplacian_coeffs(gs.stencil_offsets(lap_plan), 4)
+    h, steps = 10.0, 500
+    dt = 0.4 * h / 4500.0
+    wl = inputs.ricker(15.0, dt, steps)
+    v = inputs.velocity_field(5001, n3)
+    vt = inputs.perturbed_velocity(v)
+    wp = W.wave_plan(n3, 4, lap, h, dt, steps, (10, 128, 128), wl, 10, 25)
+    v32 = torch.from_numpy(v.astype(np.float32)).cuda()
+    vt32 = torch.from_numpy(vt.astype(np.float32)).cuda()
+    obs = torch.empty(wp.trace_shape, dtype=torch.float32, device="cuda")
+    W.wave_forward(wp, vt32, obs)
+    tr = torch.empty_like(obs)
+    J = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(n3, dtype=torch.float64, device="cuda")
+    ms_f = _time(lambda: W.wave_forward(wp, v32, tr), reps=3, warm=1)
+    ms_g = _time(lambda: W.wave_gradient(wp, v32, obs, tr, J, g), reps=3, warm=1)
+    cells = 256 ** 3
+    out.append({"workload": "3D acoustic wave 256^3, r4 Laplacian, 500 leapfrog steps",
+                "ms_forward": round(ms_f, 2), "ms_gradient": round(ms_g, 2),
+                "gradient_over_forward": round(ms_g / ms_f, 2),
+                "forward_Gcell_updates_per_s": round(cells * steps / ms_f / 1e6, 2),
+                "forward_alg_GBps": round(16 * cells * steps / (ms_f * 1e-3) / 1e9, 1),
+                "J": J.item(), "checkpoint_every": 25})
+    for row in out:
+        print(json.dumps(row), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,12 +515,17 @@ def main():
     ap.add_argument("--only", choices=["star", "box"], default=None,
                     help="profiling case: only the 1-sweep call of one stencil, no JSON line")
     ap.add_argument("--grid", type=int, default=N, help="cube side (profiling cases only)")
+    ap.add_argument("--suite", action="store_true",
+                    help="measure the other workloads (one JSON line each) instead")
     ap.add_argument("--variant", default=None,
                     help="profiling case: JSON dict of stencil_variant fields to force")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: at least 3 warm-up steps are required; using 3", file=sys.stderr)
         args.warmup = 3
+    if args.suite:
+        suite()
+        return
     if args.only is None:
         args.grid = N  # the benchmark line is always the 512^3 workload
     if args.impl == "reference":
