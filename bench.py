@@ -180,6 +180,9 @@ def bench_ours(args):
     build.build()
     import paper_2609_06694_gb300 as gs
 
+    if args.only in ("divkgrad", "wave", "batch"):
+        profile_case(args)
+        return
     W = build_workload(device, args.grid)
     stream = torch.cuda.current_stream(device)
     if args.only:
@@ -303,6 +306,55 @@ def bench_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def profile_case(args):
+    """Single-kernel profiling cases of the other workloads (no JSON benchmark line)."""
+    import torch
+
+    import paper_2609_06694_gb300 as gs
+    from paper_2609_06694_gb300 import inputs
+    from paper_2609_06694_gb300 import wave as W
+    if args.only == "divkgrad":
+        n = args.grid if args.grid != N else 384
+        plan = gs.stencil_plan(3, (n, n, n), "star", 1, "divkgrad", None, "f32", "dirichlet")
+        k = inputs.to_storage(inputs.lognormal_k(3002, (n, n, n)), "f32").cuda()
+        u = inputs.to_storage(inputs.uniform(3001, (n, n, n)), "f32").cuda()
+        y = torch.empty_like(u)
+        for _ in range(args.warmup + args.steps):
+            gs.stencil_apply_var(plan, u, [k], y, 1)
+        rc = gs.stencil_sync_status(plan)
+    elif args.only == "wave":
+        n3 = (256, 256, 256)
+        lp = gs.stencil_plan(3, n3, "star", 4, "const", np.ones(25), "f32", "dirichlet")
+        lap = inputs.laplacian_coeffs(gs.stencil_offsets(lp), 4)
+        dt = 0.4 * 10.0 / 4500.0
+        steps = 20
+        wp = W.wave_plan(n3, 4, lap, 10.0, dt, steps, (10, 128, 128),
+                         inputs.ricker(15.0, dt, steps), 10, 25)
+        v = torch.from_numpy(inputs.velocity_field(5001, n3).astype(np.float32)).cuda()
+        tr = torch.empty(wp.trace_shape, dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            W.wave_forward(wp, v, tr)
+        torch.cuda.synchronize()
+        rc = 0
+    else:
+        specs = inputs.batched_grid_specs()
+        items = []
+        for sp in specs:
+            d = (sp["ny"], sp["nx"])
+            npts = {"star": 4 * sp["radius"] + 1, "box": (2 * sp["radius"] + 1) ** 2}[sp["shape"]]
+            c = inputs.normalised_abs_weights(sp["weight_seed"], npts)
+            pl = gs.stencil_plan(2, d, sp["shape"], sp["radius"], "const", c, "f32", "dirichlet")
+            xi = inputs.to_storage(inputs.uniform(sp["input_seed"], d), "f32").cuda()
+            items.append((pl, xi, torch.empty_like(xi)))
+        batch = gs.stencil_batch_plan(items, 20)
+        for _ in range(args.warmup + args.steps):
+            gs.stencil_batch_launch(batch)
+        rc = gs.stencil_batch_status(batch)
+    print(json.dumps({"profile_case": args.only, "status": rc}))
+    if rc:
+        raise SystemExit(1)
 
 
 def _oracle_sample(seed_star=2001, seed_box=2003, nz=16):
@@ -512,7 +564,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", choices=["star", "box"], default=None,
+    ap.add_argument("--only", choices=["star", "box", "divkgrad", "wave", "batch"], default=None,
                     help="profiling case: only the 1-sweep call of one stencil, no JSON line")
     ap.add_argument("--grid", type=int, default=N, help="cube side (profiling cases only)")
     ap.add_argument("--suite", action="store_true",

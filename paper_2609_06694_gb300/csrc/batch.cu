@@ -117,8 +117,8 @@ __device__ void batch_tile(const BatchParams &P, const BatchGrid &G, const Batch
     t.th = min(P.tile_y, G.ny - tl.y0);
     t.tw = min(P.tile_x, G.nx - tl.x0);
     t.steps = k;
-    fused2d_tile<T, SHAPE, R, true>(static_cast<const T *>(src), static_cast<T *>(dst), t, buf,
-                                    [&](int idx) { return creg[idx]; });
+    fused2d_tile<T, SHAPE, R, true, 4>(static_cast<const T *>(src), static_cast<T *>(dst), t, buf,
+                                       [&](int idx) { return creg[idx]; });
 }
 
 template <typename T>
@@ -135,7 +135,7 @@ __device__ __forceinline__ void batch_tile_dt(const BatchParams &P, const BatchG
     }
 }
 
-__global__ void __launch_bounds__(256) batch_persistent_kernel(const BatchParams P) {
+__global__ void __launch_bounds__(128) batch_persistent_kernel(const BatchParams P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *buf = reinterpret_cast<float *>(smem_raw);
     for (int g = 0; g < P.groups; ++g) {
@@ -159,8 +159,8 @@ using namespace gst;
 
 struct stencil_batch_s {
     int n = 0, steps = 0, fuse = 1, groups = 0;
-    int tile_y = 32, tile_x = 128;
-    int nblocks = 0, threads = 256;
+    int tile_y = 32, tile_x = 120;  // a halo row (<= 124 cells) is one pass of 32 lanes x 4
+    int nblocks = 0, threads = 128;
     size_t smem = 0;
     BatchGrid *d_grids = nullptr;
     BatchTile *d_tiles = nullptr;
@@ -214,7 +214,7 @@ int stencil_batch_plan(stencil_batch *out, const stencil_batch_item *items, int 
     if (!b) return STENCIL_ERR_OOM;
     b->n = n;
     b->steps = steps;
-    // one step per group (a barrier between steps); tiles of 32 x 128 cells
+    // one step per group (a barrier between steps); tiles of 32 x 120 cells
     b->fuse = 1;
     b->groups = (steps + b->fuse - 1) / b->fuse;
     int max_r = 1;

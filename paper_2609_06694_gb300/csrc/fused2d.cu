@@ -6,7 +6,7 @@ namespace gst {
 
 size_t fused2d_smem_bytes(int tile_x, int tile_y, int radius, int steps) {
     const size_t h = (size_t)radius * steps;
-    return 2 * (tile_x + 2 * h) * (tile_y + 2 * h) * sizeof(float);
+    return (steps > 1 ? 2 : 1) * (tile_x + 2 * h) * (tile_y + 2 * h) * sizeof(float);
 }
 
 template <typename T, int SHAPE, int R> static int launch_fused2d_t(const Fused2DLaunch &L) {

@@ -41,57 +41,99 @@ template <typename T> __device__ __forceinline__ T load_l2(const T *p) {
     }
 }
 
-// Runs `t.steps` sweeps on one tile.  `buf` holds 2 * (th + 2H) * (tw + 2H) floats.
+// Runs `t.steps` sweeps on one tile.  `buf` holds (th + 2H) * (tw + 2H) floats, twice that
+// when t.steps > 1.
 // `coef(idx)` returns the coefficient of canonical offset idx.  All threads of the block must
 // call this; it ends with a __syncthreads().  COHERENT loads the input through L2 only.
-template <typename T, int SHAPE, int R, bool COHERENT = false, typename Coef>
+// VX: consecutive cells per lane and pass (1 suits narrow regions, 4 reuses each window row
+// for four outputs).
+template <typename T, int SHAPE, int R, bool COHERENT = false, int VX = 1, typename Coef>
 __device__ __forceinline__ void fused2d_tile(const T *__restrict__ in, T *__restrict__ out,
                                              const Fused2DTile &t, float *buf, const Coef &coef) {
+    using OT = OffsetTable<2, SHAPE, R>;
     const int H = R * t.steps;
     const int W = t.tw + 2 * H;
     const int Hh = t.th + 2 * H;
-    const int n = W * Hh;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
     const bool periodic = t.periodic != 0;
-    float *src = buf, *dst = buf + n;
+    const int gx0 = t.x0 - H, gy0 = t.y0 - H;  // grid position of region cell (0, 0)
+    const bool x_in = gx0 >= 0 && gx0 + W <= t.nx;  // every column of the region is in the grid
+    float *src = buf, *dst = buf + W * Hh;  // dst is used only when steps > 1
 
-    // load the tile with its halo (zero outside a Dirichlet grid)
-    for (int e = tid; e < n; e += nthr) {
-        int row = e / W, col = e - row * W;
-        bool ok = true;
-        int gy = wrap_or_flag(t.y0 - H + row, t.ny, periodic, ok);
-        int gx = wrap_or_flag(t.x0 - H + col, t.nx, periodic, ok);
-        const T *a = in + (size_t)gy * t.nx + gx;
-        src[e] = ok ? Storage<T>::to_float(COHERENT ? load_l2(a) : *a) : 0.0f;
+    // load the tile with its halo, one warp per row (zero outside a Dirichlet grid)
+    for (int r = warp; r < Hh; r += nwarps) {
+        bool rok = true;
+        const int gy = wrap_or_flag(gy0 + r, t.ny, periodic, rok);
+        float *srow = src + r * W;
+        if (!rok) {
+            for (int c = lane; c < W; c += 32) srow[c] = 0.0f;
+            continue;
+        }
+        const T *grow = in + (size_t)gy * t.nx;
+        if (x_in) {
+            for (int c = lane; c < W; c += 32) {
+                const T *a = grow + gx0 + c;
+                srow[c] = Storage<T>::to_float(COHERENT ? load_l2(a) : *a);
+            }
+        } else {
+            for (int c = lane; c < W; c += 32) {
+                bool ok = true;
+                const int gx = wrap_or_flag(gx0 + c, t.nx, periodic, ok);
+                const T *a = grow + gx;
+                srow[c] = ok ? Storage<T>::to_float(COHERENT ? load_l2(a) : *a) : 0.0f;
+            }
+        }
     }
     __syncthreads();
 
     for (int s = 1; s <= t.steps; ++s) {
-        const int g = R * s;  // rows/cols of the region not recomputed at this step
-        const int rw = W - 2 * g, rh = Hh - 2 * g;
-        const int rn = rw * rh;
+        const int g = R * s;  // border of the region not recomputed at this step
+        const int r1 = Hh - g, c1 = W - g;
         const bool last = (s == t.steps);
-        for (int e = tid; e < rn; e += nthr) {
-            const int row = g + e / rw, col = g + e % rw;
-            const float *c0 = src + row * W + col;
-            float v = 0.0f;
-            static_for<2 * R + 1>([&](auto dyi) {
-                constexpr int dy = decltype(dyi)::value - R;
-                static_for<2 * R + 1>([&](auto dxi) {
-                    constexpr int dx = decltype(dxi)::value - R;
-                    constexpr int idx = OffsetTable<2, SHAPE, R>::index(0, dy, dx);
-                    if constexpr (idx >= 0) v = fmaf(coef(idx), c0[dy * W + dx], v);
+        for (int r = g + warp; r < r1; r += nwarps) {
+            const int gy = gy0 + r;
+            const bool row_out = !periodic && (gy < 0 || gy >= t.ny);
+            for (int cb = g + lane * VX; cb < c1; cb += 32 * VX) {
+                float v[VX];
+#pragma unroll
+                for (int i = 0; i < VX; ++i) v[i] = 0.0f;
+                const bool full = cb + VX + R <= W;  // the whole window lies in this row
+                static_for<2 * R + 1>([&](auto dyi) {
+                    constexpr int dy = decltype(dyi)::value - R;
+                    constexpr int m = OT::tab.mdx[R][dy + R];
+                    if constexpr (m >= 0) {
+                        const float *wrow = src + (r + dy) * W + cb;
+                        float win[VX + 2 * R];
+#pragma unroll
+                        for (int i = -m; i < VX + m; ++i)
+                            win[i + R] = (full || cb + i < W) ? wrow[i] : 0.0f;
+                        static_for<2 * R + 1>([&](auto dxi) {
+                            constexpr int dx = decltype(dxi)::value - R;
+                            constexpr int idx = OT::index(0, dy, dx);
+                            if constexpr (idx >= 0) {
+                                const float c = coef(idx);
+#pragma unroll
+                                for (int i = 0; i < VX; ++i) v[i] = fmaf(c, win[i + dx + R], v[i]);
+                            }
+                        });
+                    }
                 });
-            });
-            const int gy = t.y0 - H + row, gx = t.x0 - H + col;
-            if (!periodic && (gy < 0 || gy >= t.ny || gx < 0 || gx >= t.nx)) v = 0.0f;
-            if (last) {
-                if (gy >= 0 && gy < t.ny && gx >= 0 && gx < t.nx && row >= H && row < H + t.th &&
-                    col >= H && col < H + t.tw)
-                    out[(size_t)gy * t.nx + gx] = Storage<T>::from_float(v);
-            } else {
-                dst[row * W + col] = round_to_storage<T>(v);
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    const int col = cb + i;
+                    if (col >= c1) break;
+                    const int gx = gx0 + col;
+                    if (last) {
+                        // the last step's region is exactly the output tile (inside the grid)
+                        out[(size_t)gy * t.nx + gx] = Storage<T>::from_float(v[i]);
+                    } else {
+                        const bool out_of_grid = row_out || (!periodic && !x_in &&
+                                                             (gx < 0 || gx >= t.nx));
+                        dst[r * W + col] = out_of_grid ? 0.0f : round_to_storage<T>(v[i]);
+                    }
+                }
             }
         }
         __syncthreads();

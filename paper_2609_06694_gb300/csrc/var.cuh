@@ -67,6 +67,69 @@ __device__ __forceinline__ void load_tile_plane(const T *__restrict__ field, T *
     }
 }
 
+// The same copy with per-thread chunk addresses computed once per tile (the first KMAX chunks
+// of every thread; any further chunks are addressed on the fly).  `load` works for any field
+// of the grid's shape.
+template <typename T, int R, int A, int PITCH> struct TileLoader {
+    static constexpr int KMAX = 4;
+    static constexpr int CPR = PITCH / A;
+    uint32_t dst[KMAX];
+    int src[KMAX];  // in-plane element offset, -1 = zero fill
+    int nk, nchunks, x0, y0, nx, ny, nz, rows, tid, nthr;
+    bool periodic, aligned, is3d;
+
+    __device__ __forceinline__ void init(int x0_, int y0_, int rows_, int nx_, int ny_, int nz_,
+                                         bool periodic_, bool aligned_, bool is3d_, int tid_,
+                                         int nthr_) {
+        x0 = x0_; y0 = y0_; rows = rows_; nx = nx_; ny = ny_; nz = nz_;
+        periodic = periodic_; aligned = aligned_; is3d = is3d_; tid = tid_; nthr = nthr_;
+        nchunks = CPR * rows;
+        nk = 0;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int c = tid + k * nthr;
+            dst[k] = 0;
+            src[k] = -1;
+            if (c < nchunks) {
+                const int row = c / CPR, cc = c - row * CPR;
+                bool ok = true;
+                const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
+                const int gx = wrap_or_flag(x0 - A + cc * A, nx, periodic, ok);
+                dst[k] = (uint32_t)(c * 16);
+                src[k] = ok ? gy * nx + gx : -1;
+                nk = k + 1;
+            }
+        }
+    }
+    __device__ __forceinline__ void load(const T *__restrict__ field, T *slot_smem, int zi) const {
+        if (!aligned) {
+            load_tile_plane<T, R, A, PITCH>(field, slot_smem, zi, nx, ny, nz, periodic, false, x0,
+                                            y0, rows, tid, nthr, is3d);
+            return;
+        }
+        bool zok = true;
+        const int gz = is3d ? wrap_or_flag(zi, nz, periodic, zok) : 0;
+        const T *plane = field + (size_t)gz * nx * ny;
+        const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(slot_smem));
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            if (k < nk) {
+                const bool ok = zok && src[k] >= 0;
+                cp_async16_u32(sbase + dst[k], ok ? (const void *)(plane + src[k]) : field,
+                               ok ? 16 : 0);
+            }
+        }
+        for (int c = tid + KMAX * nthr; c < nchunks; c += nthr) {
+            const int row = c / CPR, cc = c - row * CPR;
+            bool ok = zok;
+            const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
+            const int gx = wrap_or_flag(x0 - A + cc * A, nx, periodic, ok);
+            cp_async16_u32(sbase + (uint32_t)(c * 16),
+                           ok ? (const void *)(plane + (size_t)gy * nx + gx) : field, ok ? 16 : 0);
+        }
+    }
+};
+
 // VX consecutive values of a global array as floats (vector load when allowed).
 template <typename T, int VX>
 __device__ __forceinline__ void load_cells(const T *__restrict__ src, bool vec, int nvalid,
@@ -129,10 +192,11 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
     const bool vec = aligned && ox + VX <= nx;
     const int nvalid = nx - ox;
 
+    TileLoader<T, R, A, PITCH> loader;
+    loader.init(x0, y0, rows, nx, ny, nz, periodic, aligned, NDIM == 3, tid, nthr);
     auto load = [&](int zi) {
         const int slot = ((zi - z_begin + RZ) % NSLOT + NSLOT) % NSLOT;
-        load_tile_plane<T, R, A, PITCH>(p.in, smem + slot * plane_elems, zi, nx, ny, nz, periodic,
-                                        aligned, x0, y0, rows, tid, nthr, NDIM == 3);
+        loader.load(p.in, smem + slot * plane_elems, zi);
     };
     // prologue: planes z_begin-RZ .. z_begin+RZ
     for (int zi = z_begin - RZ; zi <= z_begin + RZ; ++zi) {
@@ -238,12 +302,12 @@ __global__ void __launch_bounds__(256) divkgrad_kernel(const __grid_constant__ V
     const T *kfield = p.w[0];
 
     auto slot_of = [&](int zi) { return ((zi - z_begin + RZ) % NSLOT + NSLOT) % NSLOT; };
+    TileLoader<T, R, A, PITCH> loader;
+    loader.init(x0, y0, rows, nx, ny, nz, periodic, aligned, NDIM == 3, tid, nthr);
     auto load = [&](int zi) {
         const int s = slot_of(zi);
-        load_tile_plane<T, R, A, PITCH>(p.in, su + s * plane_elems, zi, nx, ny, nz, periodic,
-                                        aligned, x0, y0, rows, tid, nthr, NDIM == 3);
-        load_tile_plane<T, R, A, PITCH>(kfield, sk + s * plane_elems, zi, nx, ny, nz, periodic,
-                                        aligned, x0, y0, rows, tid, nthr, NDIM == 3);
+        loader.load(p.in, su + s * plane_elems, zi);
+        loader.load(kfield, sk + s * plane_elems, zi);
     };
     for (int zi = z_begin - RZ; zi <= z_begin + RZ; ++zi) {
         load(zi);
@@ -263,48 +327,63 @@ __global__ void __launch_bounds__(256) divkgrad_kernel(const __grid_constant__ V
             float acc[VX];
 #pragma unroll
             for (int i = 0; i < VX; ++i) acc[i] = 0.0f;
-            // a neighbour outside a Dirichlet grid has u = 0 and k = k[p]
-            auto face = [&](int i, float un, float kn, bool inside) {
-                const float kc = k0[i + 1];
-                const float kf = inside ? 0.5f * (kc + kn) : kc;
-                const float du = (inside ? un : 0.0f) - u0[i + 1];
-                acc[i] = fmaf(kf, du, acc[i]);
+            // Each face adds (k_c + k_n) (u_n - u_c); the sum is halved at the end (exact, so
+            // this equals the half-face form bit for bit).  A neighbour outside a Dirichlet
+            // grid has u = 0 and k = k_c.  ALLIN: no neighbour of this thread's cells is
+            // outside the grid, so no face needs a select.
+            auto compute = [&](auto allin_c) {
+                constexpr bool ALLIN = decltype(allin_c)::value;
+                auto face = [&](int i, float un, float kn, bool inside) {
+                    const float kc = k0[i + 1];
+                    const bool in = ALLIN || inside;
+                    const float ssum = kc + (in ? kn : kc);
+                    const float d = (in ? un : 0.0f) - u0[i + 1];
+                    acc[i] = fmaf(ssum, d, acc[i]);
+                };
+                // axes in the oracle's order: z, y, x; within an axis the + face then the - face
+                if constexpr (NDIM == 3) {
+                    const int sp = slot_of(zo + 1) * plane_elems + off;
+                    const int sm = slot_of(zo - 1) * plane_elems + off;
+                    float up[VX], kp[VX], um[VX], km[VX];
+                    load_span<T, 0, VX, 0>(su + sp, up);
+                    load_span<T, 0, VX, 0>(sk + sp, kp);
+                    load_span<T, 0, VX, 0>(su + sm, um);
+                    load_span<T, 0, VX, 0>(sk + sm, km);
+                    const bool inp = periodic || zo + 1 < nz, inm = periodic || zo - 1 >= 0;
+#pragma unroll
+                    for (int i = 0; i < VX; ++i) {
+                        face(i, up[i], kp[i], inp);
+                        face(i, um[i], km[i], inm);
+                    }
+                }
+                {
+                    float up[VX], kp[VX], um[VX], km[VX];
+                    load_span<T, 0, VX, 0>(su + s0 + PITCH, up);
+                    load_span<T, 0, VX, 0>(sk + s0 + PITCH, kp);
+                    load_span<T, 0, VX, 0>(su + s0 - PITCH, um);
+                    load_span<T, 0, VX, 0>(sk + s0 - PITCH, km);
+                    const bool inp = periodic || oy + 1 < ny, inm = periodic || oy - 1 >= 0;
+#pragma unroll
+                    for (int i = 0; i < VX; ++i) {
+                        face(i, up[i], kp[i], inp);
+                        face(i, um[i], km[i], inm);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    const bool inp = periodic || ox + i + 1 < nx, inm = periodic || ox + i - 1 >= 0;
+                    face(i, u0[i + 2], k0[i + 2], inp);
+                    face(i, u0[i], k0[i], inm);
+                }
             };
-            // axes in the oracle's order: z, y, x; within an axis the + face then the - face
-            if constexpr (NDIM == 3) {
-                const int sp = slot_of(zo + 1) * plane_elems + off;
-                const int sm = slot_of(zo - 1) * plane_elems + off;
-                float up[VX], kp[VX], um[VX], km[VX];
-                load_span<T, 0, VX, 0>(su + sp, up);
-                load_span<T, 0, VX, 0>(sk + sp, kp);
-                load_span<T, 0, VX, 0>(su + sm, um);
-                load_span<T, 0, VX, 0>(sk + sm, km);
-                const bool inp = periodic || zo + 1 < nz, inm = periodic || zo - 1 >= 0;
+            const bool all_in = periodic || (ox > 0 && ox + VX < nx && oy > 0 && oy + 1 < ny &&
+                                             (NDIM == 2 || (zo > 0 && zo + 1 < nz)));
+            if (all_in)
+                compute(std::true_type{});
+            else
+                compute(std::false_type{});
 #pragma unroll
-                for (int i = 0; i < VX; ++i) {
-                    face(i, up[i], kp[i], inp);
-                    face(i, um[i], km[i], inm);
-                }
-            }
-            {
-                float up[VX], kp[VX], um[VX], km[VX];
-                load_span<T, 0, VX, 0>(su + off + slot_of(zo) * plane_elems + PITCH, up);
-                load_span<T, 0, VX, 0>(sk + off + slot_of(zo) * plane_elems + PITCH, kp);
-                load_span<T, 0, VX, 0>(su + off + slot_of(zo) * plane_elems - PITCH, um);
-                load_span<T, 0, VX, 0>(sk + off + slot_of(zo) * plane_elems - PITCH, km);
-                const bool inp = periodic || oy + 1 < ny, inm = periodic || oy - 1 >= 0;
-#pragma unroll
-                for (int i = 0; i < VX; ++i) {
-                    face(i, up[i], kp[i], inp);
-                    face(i, um[i], km[i], inm);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < VX; ++i) {
-                const bool inp = periodic || ox + i + 1 < nx, inm = periodic || ox + i - 1 >= 0;
-                face(i, u0[i + 2], k0[i + 2], inp);
-                face(i, u0[i], k0[i], inm);
-            }
+            for (int i = 0; i < VX; ++i) acc[i] *= 0.5f;
             store_cells<T, VX>(p.out + (size_t)zo * pstride + (size_t)oy * nx + ox, vec, nvalid,
                                acc);
         }

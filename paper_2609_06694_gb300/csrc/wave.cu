@@ -73,10 +73,9 @@ __global__ void __launch_bounds__(256) wave_step_kernel(const __grid_constant__ 
     for (int i = 0; i < OT::count; ++i) creg[i] = p.c[i];
 
     auto slot_of = [&](int zi) { return ((zi - z_begin + R) % NSLOT + NSLOT) % NSLOT; };
-    auto load = [&](int zi) {
-        load_tile_plane<float, R, A, PITCH>(p.u, smem + slot_of(zi) * plane_elems, zi, nx, ny, nz,
-                                            false, aligned, x0, y0, rows, tid, nthr, true);
-    };
+    TileLoader<float, R, A, PITCH> loader;
+    loader.init(x0, y0, rows, nx, ny, nz, false, aligned, true, tid, nthr);
+    auto load = [&](int zi) { loader.load(p.u, smem + slot_of(zi) * plane_elems, zi); };
     for (int zi = z_begin - R; zi <= z_begin + R; ++zi) {
         load(zi);
         cp_async_commit();
@@ -88,6 +87,12 @@ __global__ void __launch_bounds__(256) wave_step_kernel(const __grid_constant__ 
         cp_async_wait<1>();
         __syncthreads();
         if (oy < ny && ox < nx) {
+            // pointwise operands first: their global-load latency overlaps the stencil below
+            const size_t base = (size_t)zo * pstride + (size_t)oy * nx + ox;
+            float up[VX], av[VX], lu[VX];
+            load_cells<float, VX>(p.uprev + base, vec, nvalid, up);
+            load_cells<float, VX>(p.a + base, vec, nvalid, av);
+            if constexpr (ADJ) load_cells<float, VX>(p.lu_prev + base, vec, nvalid, lu);
             float L[VX], uc[VX];
 #pragma unroll
             for (int i = 0; i < VX; ++i) L[i] = 0.0f;
@@ -117,10 +122,7 @@ __global__ void __launch_bounds__(256) wave_step_kernel(const __grid_constant__ 
                     }
                 });
             });
-            const size_t base = (size_t)zo * pstride + (size_t)oy * nx + ox;
-            float up[VX], av[VX], un[VX];
-            load_cells<float, VX>(p.uprev + base, vec, nvalid, up);
-            load_cells<float, VX>(p.a + base, vec, nvalid, av);
+            float un[VX];
 #pragma unroll
             for (int i = 0; i < VX; ++i) un[i] = fmaf(av[i], L[i], 2.0f * uc[i] - up[i]);
             if constexpr (!ADJ) {
@@ -142,8 +144,6 @@ __global__ void __launch_bounds__(256) wave_step_kernel(const __grid_constant__ 
                     for (int i = 0; i < VX; ++i) un[i] = fmaf(av[i], rt[i] - ro[i], un[i]);
                 }
                 store_cells<float, VX>(p.unext + base, vec, nvalid, un);
-                float lu[VX];
-                load_cells<float, VX>(p.lu_prev + base, vec, nvalid, lu);
 #pragma unroll
                 for (int i = 0; i < VX; ++i)
                     if (i < nvalid) p.G[base + i] += (double)un[i] * (double)lu[i];
