@@ -203,10 +203,12 @@ typedef struct {
     int block_x; /* threads along x                                                             */
     int block_y; /* threads along y                                                             */
     int vec_y;   /* rows per thread                                                             */
-    int z_chunk; /* planes per CTA (3D streaming); 0 = whole extent                             */
+    int z_chunk; /* planes per CTA (3D streaming); 0 = an equal share per resident CTA          */
     int fuse;    /* time steps fused per launch                                                 */
     int tile_x;  /* output tile width of fused 2D kernels (0 = default)                         */
     int tile_y;  /* output tile height of fused 2D kernels (0 = default)                        */
+    int stages;  /* shared-memory ring depth of the streaming loader, 2..16 planes; 0 = as deep
+                    as the shared memory left by the CTAs that fit on an SM allows             */
 } stencil_variant;
 
 #define STENCIL_FAMILY_STREAM 1 /* one sweep per launch, z-streaming tiles, cp.async pipeline  */
@@ -220,7 +222,8 @@ int stencil_plan_set_variant(stencil_handle h, const stencil_variant *v);
 
 /* stencil_load_dispatch_map -- replace the process-wide dispatch map with the one in the
  * text file at `path` (format: lines "ndim shape radius dtype boundary kind size_class :
- * family block_x block_y vec_y z_chunk fuse tile_x tile_y", '#' comments).  Plans created
+ * family block_x block_y vec_y z_chunk fuse tile_x tile_y [stages]", '#' comments; a
+ * missing stages field reads as 0).  Plans created
  * afterwards use it.  NULL restores the built-in defaults.  If the environment variable
  * STENCIL_DISPATCH_MAP names a file, it is loaded once before the first stencil_plan. */
 int stencil_load_dispatch_map(const char *path);

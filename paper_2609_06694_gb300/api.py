@@ -34,7 +34,7 @@ class StencilError(RuntimeError):
 class stencil_variant(ctypes.Structure):
     _fields_ = [("family", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
                 ("vec_y", ctypes.c_int), ("z_chunk", ctypes.c_int), ("fuse", ctypes.c_int),
-                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int)]
+                ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int), ("stages", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

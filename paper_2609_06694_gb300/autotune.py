@@ -39,21 +39,29 @@ def stream_candidates(ndim, shape, radius, dtype, quick=False):
     vys = [1, 2] if (ndim == 2 or shape == "star" or radius <= 2) else [1]
     if radius == 1:
         vys.append(4)
-    bys = [b for b in (1, 2, 4, 8, 16) if 32 <= bx * b <= 256 and (bx * b) % 32 == 0]
     zcs = [0] if ndim == 2 else ([0, 64] if quick else [0, 32, 64, 128])
-    for vy, by, zc in itertools.product(vys, bys, zcs):
-        out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=vy, z_chunk=zc,
-                        fuse=1, tile_x=0, tile_y=0))
+    # ring depth: 0 fills the shared memory the resident CTAs leave; 4 is the shallow ring
+    stages = [0] if ndim == 2 else ([0] if quick else [0, 4])
+    for vy in vys:
+        # consumer threads per CTA (plus the producer warp): up to 224, or 480 for 3D stars
+        # of radius >= 3 with one row per thread
+        tmax = 480 if (ndim == 3 and shape == "star" and radius >= 3 and vy == 1) else 224
+        heights = (1, 2, 3, 4, 6, 7, 8, 12, 14, 15) if not quick else (2, 4, 7)
+        bys = [b for b in heights if 32 <= bx * b <= tmax and (bx * b) % 32 == 0]
+        for by, zc, ns in itertools.product(bys, zcs, stages):
+            out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=vy,
+                            z_chunk=zc, fuse=1, tile_x=0, tile_y=0, stages=ns))
     return out
 
 
 def fused2d_candidates(radius, steps):
     out = []
     for fuse in sorted({1, 2, 4, 5, 8, 10} & set(range(1, steps + 1)) | {steps}):
-        for tile in ((32, 32), (64, 32), (64, 64), (128, 32)):
+        for tile in ((32, 16), (32, 32), (64, 16), (64, 32), (64, 64), (128, 32)):
             for threads in (128, 256):
                 out.append(dict(family=gs.FAMILY_FUSED2D, block_x=threads, block_y=1, vec_y=1,
-                                z_chunk=0, fuse=fuse, tile_x=tile[0], tile_y=tile[1]))
+                                z_chunk=0, fuse=fuse, tile_x=tile[0], tile_y=tile[1],
+                                stages=0))
     return out
 
 
@@ -159,7 +167,7 @@ def main():
     lines = ["# dispatch map written by paper_2609_06694_gb300.autotune on "
              + torch.cuda.get_device_name(0),
              "# ndim shape radius dtype boundary kind size_class : "
-             "family block_x block_y vec_y z_chunk fuse tile_x tile_y"]
+             "family block_x block_y vec_y z_chunk fuse tile_x tile_y stages"]
     evidence = []
     for ndim, dims, shape, r, dtype, bc, steps in tuning_set(args.quick):
         best, ev = tune_key(ndim, dims, shape, r, dtype, bc, steps, args.quick)
@@ -167,8 +175,8 @@ def main():
             continue
         cls = gs.stencil_size_class(int(np.prod(dims)))
         key = [ndim, SHAPE_ID[shape], r, DTYPE_ID[dtype], BC_ID[bc], KIND_ID["const"], cls]
-        val = [best[k] for k in ("family", "block_x", "block_y", "vec_y", "z_chunk", "fuse",
-                                 "tile_x", "tile_y")]
+        val = [best.get(k, 0) for k in ("family", "block_x", "block_y", "vec_y", "z_chunk",
+                                        "fuse", "tile_x", "tile_y", "stages")]
         lines.append(" ".join(map(str, key)) + " : " + " ".join(map(str, val)))
         evidence.append({"key": {"ndim": ndim, "dims": list(dims), "shape": shape, "radius": r,
                                  "dtype": dtype, "boundary": bc, "steps": steps,

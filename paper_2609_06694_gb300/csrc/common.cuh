@@ -196,6 +196,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
         if ((i & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
+// As mbar_wait_bounded, but also gives up (false) once *abort_flag is nonzero: another warp of
+// the CTA has stopped, so the arrival may never come.
+__device__ __forceinline__ bool mbar_wait_abortable(uint32_t bar, uint32_t parity,
+                                                    unsigned long long limit_ns,
+                                                    const volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned int i = 1;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 0 && (*abort_flag != 0 || globaltimer_ns() - t0 > limit_ns)) return false;
+    }
+}
 // Order earlier generic-proxy accesses of shared memory before later async-proxy writes.
 __device__ __forceinline__ void fence_proxy_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");

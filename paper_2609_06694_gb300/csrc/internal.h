@@ -17,15 +17,17 @@ struct StreamLaunch {
     const void *in;
     void *out;
     int block_x, block_y, vec_y, z_chunk;
+    int stages = 0;          // ring depth (0 = fill the shared memory, see stream_stages)
     int use_tma = 1;         // 0 forces the cp.async loader (tensor maps are used when legal)
     int *err;                // device error word or null
     cudaStream_t stream;
 };
 
 // Returns 0, or a negative STENCIL_ERR_* code.  One per storage type and dimension.
-// Largest CTA of a streaming kernel (kept in step with StreamKernel::MAX_THREADS).
+// Most consumer threads of a streaming kernel's CTA (kept in step with
+// StreamKernel::MAX_THREADS); the CTA adds one producer warp.
 constexpr int stream_max_threads(int ndim, int shape, int radius, int vec_y) {
-    return (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 1) ? 512 : 256;
+    return (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 1) ? 480 : 224;
 }
 
 // Defined in stream_<dtype>_<ndim>d_<shape>.cu.

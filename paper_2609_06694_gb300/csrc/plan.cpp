@@ -72,10 +72,16 @@ static stencil_variant default_variant(const stencil_plan_s &p) {
     const int vx = 16 / es;
     v.family = STENCIL_FAMILY_STREAM;
     v.block_x = 128 / vx;  // 128-cell tiles in x
-    v.block_y = 256 / v.block_x;
+    v.block_y = 128 / v.block_x;  // 128 consumer threads
     v.vec_y = 1;
     v.z_chunk = 0;  // balanced persistent split
     v.fuse = 1;
+    if (p.kind != STENCIL_CONST) {
+        // variable coefficients: one output row per thread, 64-plane z chunks
+        v.block_y = (p.kind == STENCIL_DIVKGRAD ? 192 : 128) / v.block_x;
+        v.z_chunk = 64;
+        return v;
+    }
     if (p.ndim == 3) {
         // two rows per thread while the partial-sum queue stays small
         if (stream_vy_compiled(3, p.shape, p.radius, 2) && p.radius <= 2) {
@@ -116,6 +122,15 @@ static bool lookup_map(const stencil_plan_s &p, stencil_variant *out) {
 }
 
 int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
+    if (p.kind != STENCIL_CONST) {
+        // variable-coefficient kernels: 128-cell tiles, block_y rows of one output row per
+        // thread (at most 224 threads), z chunks of z_chunk planes (0 = whole columns)
+        if (v.family != STENCIL_FAMILY_STREAM || v.vec_y != 1 || v.fuse != 1 ||
+            v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
+            v.block_x * v.block_y > 224 || (v.block_x * v.block_y) % 32 != 0 || v.z_chunk < 0)
+            return STENCIL_ERR_BADARG;
+        return STENCIL_OK;
+    }
     if (v.family == STENCIL_FAMILY_STREAM) {
         // tiles are 128 cells wide: one 16-byte vector of cells per thread along x
         if (v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
@@ -125,6 +140,7 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
         if (!stream_vy_compiled(p.ndim, p.shape, p.radius, v.vec_y))
             return STENCIL_ERR_UNSUPPORTED;
         if (v.z_chunk < 0 || v.fuse != 1) return STENCIL_ERR_BADARG;
+        if (v.stages != 0 && (v.stages < 2 || v.stages > 16)) return STENCIL_ERR_BADARG;
         return STENCIL_OK;
     }
     if (v.family == STENCIL_FAMILY_FUSED2D) {
@@ -202,6 +218,7 @@ static int launch_group(stencil_plan_s &p, const float *cf, const void *src, voi
     L.block_y = v.block_y;
     L.vec_y = v.vec_y;
     L.z_chunk = v.z_chunk;
+    L.stages = v.stages;
     L.err = nullptr;
     L.stream = s;
     return map_launch_rc(launch_stream(L));
@@ -442,11 +459,11 @@ int stencil_load_dispatch_map(const char *path) {
             if (hash) *hash = 0;
             MapEntry e;
             std::memset(&e, 0, sizeof(e));
-            int n = std::sscanf(line, "%d %d %d %d %d %d %d : %d %d %d %d %d %d %d %d", &e.key[0],
-                                &e.key[1], &e.key[2], &e.key[3], &e.key[4], &e.key[5], &e.key[6],
-                                &e.v.family, &e.v.block_x, &e.v.block_y, &e.v.vec_y,
-                                &e.v.z_chunk, &e.v.fuse, &e.v.tile_x, &e.v.tile_y);
-            if (n == 15) {
+            int n = std::sscanf(line, "%d %d %d %d %d %d %d : %d %d %d %d %d %d %d %d %d",
+                                &e.key[0], &e.key[1], &e.key[2], &e.key[3], &e.key[4], &e.key[5],
+                                &e.key[6], &e.v.family, &e.v.block_x, &e.v.block_y, &e.v.vec_y,
+                                &e.v.z_chunk, &e.v.fuse, &e.v.tile_x, &e.v.tile_y, &e.v.stages);
+            if (n == 15 || n == 16) {  // the ring depth is optional (0 = automatic)
                 entries.push_back(e);
             } else {
                 bool blank = true;
@@ -487,8 +504,8 @@ static int run_var_steps(stencil_plan_s &p, const void *in, const void *const *a
     L.periodic = p.boundary == STENCIL_PERIODIC;
     L.arrays = arrays;
     L.narrays = p.kind == STENCIL_DIVKGRAD ? 1 : (int)p.npts;
-    L.block_y = 8;
-    L.z_chunk = 64;
+    L.block_y = p.variant.block_y;
+    L.z_chunk = p.variant.z_chunk;
     L.stream = s;
     const void *src = in;
     for (int g = 0; g < steps; ++g) {

@@ -1,0 +1,376 @@
+// The plane ring shared by the streaming kernels: a CTA walks z-planes of a tile; one producer
+// warp keeps a ring of shared-memory slots filled with the input planes (NF fields per plane,
+// each a tile plus an R-row halo in y and one 16-byte chunk of halo in x) while the consumer
+// warps compute.  Each slot has three mbarriers:
+//   full  -- the plane is in the slot (32 arrivals of the producer warp, plus copied bytes),
+//   empty -- every consumer warp has finished reading it (one arrival per consumer warp),
+//   tma   -- its tensor copies have landed (periodic tiles that still need patches).
+// After set-up the warps never meet at a CTA-wide barrier: consumers drift apart by up to
+// nstage - 1 planes and hide one another's latencies.  Every wait is bounded by
+// %globaltimer; a wait that gives up raises the CTA's abort flag and the device error word.
+#pragma once
+
+#include "common.cuh"
+
+namespace gst {
+
+constexpr int kMaxStages = 16;   // ring slots
+constexpr int kMaxPatches = 256; // wrapped 16-byte chunks patched per plane
+constexpr unsigned long long kRingWaitNs = 2000000000ull;  // bounded waits: 2 s
+
+// Shared-memory layout: nstage slots of NF fields, then full/empty/tma mbarriers, the abort
+// flag and the patch list.
+struct RingLayout {
+    uint32_t field_bytes;  // one field of one plane (128-byte multiple)
+    uint32_t slot_bytes;   // NF fields
+    int ns;
+    __host__ __device__ static constexpr uint32_t field_size(int pitch, int rows, int es) {
+        return (uint32_t)(((size_t)pitch * rows * es + 127) / 128 * 128);
+    }
+    __host__ __device__ static constexpr size_t bytes(uint32_t slot_bytes, int ns) {
+        return (size_t)ns * (slot_bytes + 24) + 16 + 8 * kMaxPatches;
+    }
+};
+
+struct Ring {
+    unsigned char *base;
+    uint32_t base_u32, field_bytes, slot_bytes;
+    int ns;
+    uint32_t full_u32, empty_u32, tma_u32;
+    volatile int *abort_flag;
+    uint2 *plist;
+
+    __device__ __forceinline__ void setup(unsigned char *smem, uint32_t fbytes, int nf, int nstage) {
+        base = smem;
+        base_u32 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+        field_bytes = fbytes;
+        slot_bytes = fbytes * nf;
+        ns = nstage;
+        full_u32 = base_u32 + (uint32_t)ns * slot_bytes;
+        empty_u32 = full_u32 + 8u * (uint32_t)ns;
+        tma_u32 = empty_u32 + 8u * (uint32_t)ns;
+        abort_flag = reinterpret_cast<volatile int *>(smem + (size_t)ns * slot_bytes + 24 * ns);
+        plist = reinterpret_cast<uint2 *>(smem + (size_t)ns * slot_bytes + 24 * ns + 16);
+    }
+    // thread 0, before the CTA's only __syncthreads
+    __device__ __forceinline__ void init(int consumer_warps) const {
+        for (int i = 0; i < ns; ++i) {
+            mbar_init(full_u32 + 8u * i, 32u);                       // the producer warp
+            mbar_init(empty_u32 + 8u * i, (uint32_t)consumer_warps);  // one per consumer warp
+            mbar_init(tma_u32 + 8u * i, 1u);                         // the producer's lane 0
+        }
+        *abort_flag = 0;
+        mbar_init_fence();
+    }
+    __device__ __forceinline__ const unsigned char *slot_ptr(int slot) const {
+        return base + (size_t)slot * slot_bytes;
+    }
+    // consumers: wait (warp-uniformly) for the plane in `slot`; false once a wait gives up
+    __device__ __forceinline__ bool wait_full(int slot, uint32_t phase) const {
+        return __all_sync(0xffffffffu, mbar_wait_abortable(full_u32 + 8u * slot, phase,
+                                                            kRingWaitNs, abort_flag));
+    }
+    // consumers: this warp has read `slot`
+    __device__ __forceinline__ void release(int slot, int lane) const {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty_u32 + 8u * slot);
+    }
+    __device__ __forceinline__ void fail(int *err, int lane) const {
+        *abort_flag = 1;
+        if (lane == 0) latch_error(err, kErrTimeout);
+    }
+};
+
+// Ring position of a plane sequence: plane k of it sits in slot k mod ns, pass parity
+// (k / ns) mod 2.
+struct RingPos {
+    int slot = 0;
+    uint32_t phase = 0;
+    __device__ __forceinline__ void advance(int ns) {
+        if (++slot == ns) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
+
+// A CTA's work: planes [w_first, w_end) of the flattened (tile, z) sequence (tiles in
+// row-major order, z fastest), possibly spanning several tiles; each piece is one z-stream
+// of a tile, read with RZ extra planes on each side.
+struct RingPiece {
+    int x0, y0, z_begin, z_end, zs, zl;
+};
+struct RingWork {
+    long long w_first, w_end;
+    int nzp, tiles_x, TX, TY, RZ;
+    __device__ __forceinline__ void setup(int tiles_x_, int tiles_y, int nz, int work, int TX_,
+                                          int TY_, int RZ_) {
+        tiles_x = tiles_x_;
+        nzp = nz;
+        TX = TX_;
+        TY = TY_;
+        RZ = RZ_;
+        const long long total = (long long)tiles_x_ * tiles_y * nz;
+        w_first = (long long)blockIdx.x * work;
+        w_end = min(total, w_first + (long long)work);
+    }
+    __device__ __forceinline__ RingPiece piece_at(long long w) const {
+        RingPiece q;
+        const int tile = (int)(w / nzp);
+        q.z_begin = (int)(w % nzp);
+        q.z_end = (int)min((long long)nzp, (long long)q.z_begin + (w_end - w));
+        const int tix = tile % tiles_x, tiy = tile / tiles_x;
+        q.x0 = tix * TX;
+        q.y0 = tiy * TY;
+        q.zs = q.z_begin - RZ;
+        q.zl = q.z_end + RZ;
+        return q;
+    }
+};
+
+// What the producer copies: NF fields of the grid (nz x ny x nx, x fastest) and, when rows
+// are 16-byte aligned and the driver could encode them, one 3D tensor map per field with the
+// box (PITCH, rows, 1).
+template <typename T, int NF> struct RingSource {
+    const CUtensorMap *tmap;  // NF maps (kernel parameters)
+    const T *const *field;    // NF pointers
+    int nx, ny, nz;
+    bool periodic, aligned, use_tma;
+    int rows;
+};
+
+// The producer warp: fills slot k with plane k of the CTA's sequence once every consumer warp
+// has released plane k - ns, then exits after the copies still in flight have landed.
+//  mode 2, TMA: lane 0 announces the bytes and issues one 3D tensor copy per field; the
+//    hardware zero-fills everything outside the grid (Dirichlet ghosts).
+//  mode 4, TMA + patches: a tile into which a periodic grid wraps takes the same tensor
+//    copies, on the slot's "tma" barrier; kLag planes later, once they have landed, the lanes
+//    copy the wrapped 16-byte chunks (whole rows above or below the grid, single chunks left
+//    or right of it) over the zero fill with cp.async and arrive on the full barrier when
+//    those have landed.
+//  mode 3, bulk rows: tiles with more wrapped chunks than the patch list holds (grids
+//    narrower than a tile): one bulk copy per contiguous segment of each row.
+//  mode 1, cp.async: no tensor map: 16-byte chunks of whole rows, wrapping or zero-filling.
+//  mode 0: element copies (rows not 16-byte aligned).
+// Field f of a slot starts f * field_bytes into it; rows are PITCH elements apart and the
+// tile's column 0 sits A elements into a row.
+template <typename T, int NF, int NDIM, int R, int A, int PITCH, int TX>
+__device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, NF> &src,
+                                             const RingWork &wk, int *err, int lane) {
+    constexpr int ES = (int)sizeof(T);
+    constexpr int CPR = PITCH / A;  // 16-byte chunks per shared-memory row
+    const int nx = src.nx, ny = src.ny, rows = src.rows, ns = g.ns;
+    const bool periodic = src.periodic;
+    const size_t plane_stride = (size_t)nx * ny;
+    const uint32_t plane_bytes = (uint32_t)(PITCH * rows * ES);
+    const int kLag = min(2, ns - 1);
+    RingPos pos;
+    bool ok = true;
+    int issued = 0;      // planes issued so far (for the final drain)
+    int pslot = 0;       // ring slot of the next plane to publish in mode 4
+    uint32_t tbits = 0;  // parity of each slot's next "tma" phase
+    int unpub = 0;       // mode-4 planes issued but not yet published
+    auto wait_all = [&](uint32_t bar, uint32_t parity) {
+        // the lanes agree on the outcome, so the warp never splits
+        return __all_sync(0xffffffffu,
+                          mbar_wait_abortable(bar, parity, kRingWaitNs, g.abort_flag));
+    };
+    for (long long w = wk.w_first; w < wk.w_end && ok;) {
+        const RingPiece q = wk.piece_at(w);
+        w += q.z_end - q.z_begin;
+        // Chunks a periodic grid wraps into the tile: every chunk of the rows above the grid
+        // (rows < lo_row) and below it (rows >= hi_row), then, in the rows between, the chunks
+        // left of x = 0 (chunks < lo_chk) and right of nx (chunks >= hi_chk).
+        const int lo_row = max(0, R - q.y0);
+        const int hi_row = min(rows, max(0, ny - (q.y0 - R)));
+        const int lo_chk = max(0, (A - q.x0 + A - 1) / A);
+        const int hi_chk = min(CPR, max(0, (nx - (q.x0 - A) + A - 1) / A));
+        const int nrow_oob = lo_row + (rows - hi_row);
+        const int nwc = lo_chk + (CPR - hi_chk);
+        const int npatch = nrow_oob * CPR + (hi_row - lo_row) * nwc;
+        int mode;
+        if (!src.use_tma) mode = src.aligned ? 1 : 0;
+        else if (!periodic || npatch == 0) mode = 2;
+        else if (npatch <= kMaxPatches && hi_row >= lo_row) mode = 4;
+        else mode = 3;
+        if (mode == 4) {
+            // every publish of the previous piece is done: the list is free
+            for (int i = lane; i < npatch; i += 32) {
+                int row, cc;
+                if (i < nrow_oob * CPR) {
+                    const int qr = i / CPR;
+                    row = qr < lo_row ? qr : hi_row + (qr - lo_row);
+                    cc = i - qr * CPR;
+                } else {
+                    const int j = i - nrow_oob * CPR;  // here nwc > 0
+                    const int qr = j / nwc, e = j - qr * nwc;
+                    row = lo_row + qr;
+                    cc = e < lo_chk ? e : hi_chk + (e - lo_chk);
+                }
+                bool wok = true;
+                const int gy = wrap_or_flag(q.y0 - R + row, ny, true, wok);
+                const int gx = wrap_or_flag(q.x0 - A + cc * A, nx, true, wok);
+                g.plist[i] =
+                    make_uint2((uint32_t)((row * CPR + cc) * 16), (uint32_t)(gy * nx + gx));
+            }
+            __syncwarp();
+        }
+
+        // mode 4: plane zpl's tensor copies have landed -> patch them and release the plane
+        auto publish = [&](int zpl) -> bool {
+            if (!wait_all(g.tma_u32 + 8u * pslot, (tbits >> pslot) & 1u)) return false;
+            tbits ^= 1u << pslot;
+            --unpub;
+            bool zok = true;
+            const int gz = (NDIM == 3) ? wrap_or_flag(zpl, src.nz, true, zok) : 0;
+            const uint32_t sbase = g.base_u32 + (uint32_t)pslot * g.slot_bytes;
+            for (int i = lane; i < npatch; i += 32) {
+                const uint2 e = g.plist[i];
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    cp_async16_u32(sbase + f * g.field_bytes + e.x,
+                                   src.field[f] + (size_t)gz * plane_stride + (int)e.y, 16);
+            }
+            cp_async_mbar_arrive_noinc(g.full_u32 + 8u * pslot);
+            if (++pslot == ns) pslot = 0;
+            return true;
+        };
+        // load plane zi into the slot the ring has reached (already released)
+        auto issue = [&](int zi) {
+            bool zok = true;
+            const int gz = (NDIM == 3) ? wrap_or_flag(zi, src.nz, periodic, zok) : 0;
+            const uint32_t bar = g.full_u32 + 8u * pos.slot;
+            const uint32_t sbase = g.base_u32 + (uint32_t)pos.slot * g.slot_bytes;
+            if (mode == 2 || mode == 4) {
+                if (lane == 0) {
+                    fence_proxy_async_shared();  // consumers' reads of this slot come first
+                    const uint32_t tb = mode == 2 ? bar : g.tma_u32 + 8u * pos.slot;
+                    mbar_arrive_expect_tx(tb, NF * plane_bytes);
+                    const int zc = (NDIM == 3) ? (periodic ? gz : zi) : 0;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        tma_load_3d(sbase + f * g.field_bytes, &src.tmap[f], q.x0 - A, q.y0 - R,
+                                    zc, tb);
+                } else if (mode == 2) {
+                    mbar_arrive(bar);
+                }
+                if (mode == 4) ++unpub;
+            } else if (mode == 3) {
+                // every smem row is one to a few contiguous, 16-byte aligned segments of a
+                // (wrapped) grid row: the lanes take the rows and copy the segments in bulk
+                if (lane == 0) mbar_arrive_expect_tx(bar, NF * plane_bytes);
+                __syncwarp();  // the byte count is announced before any copy can land
+                fence_proxy_async_shared();
+                for (int row = lane; row < rows; row += 32) {
+                    bool rok = true;
+                    const int gy = wrap_or_flag(q.y0 - R + row, ny, true, rok);
+                    const size_t roff = (size_t)gz * plane_stride + (size_t)gy * nx;
+                    const uint32_t drow = sbase + (uint32_t)(row * PITCH * ES);
+                    for (int col = 0; col < PITCH;) {
+                        int gx = (q.x0 - A + col) % nx;
+                        if (gx < 0) gx += nx;
+                        const int len = min(PITCH - col, nx - gx);
+#pragma unroll
+                        for (int f = 0; f < NF; ++f)
+                            bulk_copy_g2s(drow + f * g.field_bytes + (uint32_t)(col * ES),
+                                          src.field[f] + roff + gx, (uint32_t)(len * ES), bar);
+                        col += len;
+                    }
+                }
+                if (lane != 0) mbar_arrive(bar);
+            } else if (mode == 1) {
+                // lane L copies chunk columns L and L + 32 of every row (those < CPR)
+                bool cok0 = true, cok1 = (lane + 32 < CPR);
+                const int gx0 = lane < CPR ? wrap_or_flag(q.x0 - A + lane * A, nx, periodic, cok0)
+                                           : 0;
+                const int gx1 =
+                    cok1 ? wrap_or_flag(q.x0 - A + (lane + 32) * A, nx, periodic, cok1) : 0;
+                for (int row = 0; row < rows; ++row) {
+                    bool rok = zok;
+                    const int gy = wrap_or_flag(q.y0 - R + row, ny, periodic, rok);
+                    const size_t roff = (size_t)gz * plane_stride + (size_t)gy * nx;
+                    const uint32_t drow = sbase + (uint32_t)(row * PITCH * ES);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const T *fs = src.field[f];
+                        if (lane < CPR) {
+                            const bool ok0 = rok && cok0;
+                            cp_async16_u32(drow + f * g.field_bytes + 16u * lane,
+                                           ok0 ? fs + roff + gx0 : fs, ok0 ? 16 : 0);
+                        }
+                        if (lane + 32 < CPR) {
+                            const bool ok1 = rok && cok1;
+                            cp_async16_u32(drow + f * g.field_bytes + 16u * (lane + 32),
+                                           ok1 ? fs + roff + gx1 : fs, ok1 ? 16 : 0);
+                        }
+                    }
+                }
+                cp_async_mbar_arrive_noinc(bar);
+            } else {
+                // only the cells the stencil reads (x0-R .. x0+TX+R)
+                const int wcols = TX + 2 * R;
+                for (int row = 0; row < rows; ++row) {
+                    bool rok = zok;
+                    const int gy = wrap_or_flag(q.y0 - R + row, ny, periodic, rok);
+                    for (int col = lane; col < wcols; col += 32) {
+                        bool ok2 = rok;
+                        const int gx = wrap_or_flag(q.x0 - R + col, nx, periodic, ok2);
+                        const size_t gi = (size_t)gz * plane_stride + (size_t)gy * nx + gx;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            T *dst = reinterpret_cast<T *>(g.base + (size_t)pos.slot * g.slot_bytes +
+                                                           f * g.field_bytes);
+                            dst[row * PITCH + (A - R) + col] =
+                                ok2 ? src.field[f][gi] : Storage<T>::from_float(0.0f);
+                        }
+                    }
+                }
+                mbar_arrive(bar);
+            }
+            ++issued;
+            pos.advance(ns);
+        };
+
+        pslot = pos.slot;
+        int zp = q.zs;  // next plane of this piece to publish (mode 4)
+        for (int zi = q.zs; zi < q.zl; ++zi) {
+            if (!wait_all(g.empty_u32 + 8u * pos.slot, pos.phase ^ 1u)) {
+                ok = false;
+                break;
+            }
+            issue(zi);
+            // mode 4: publish the plane issued kLag planes ago (its copy has had time to land)
+            if (mode == 4 && zi + 1 - zp > kLag) {
+                if (!publish(zp)) {
+                    ok = false;
+                    break;
+                }
+                ++zp;
+            }
+        }
+        while (ok && mode == 4 && zp < q.zl) {
+            if (!publish(zp)) {
+                ok = false;
+                break;
+            }
+            ++zp;
+        }
+    }
+    if (!ok) g.fail(err, lane);
+    // Whatever the consumers do, every copy still in flight lands before the CTA can exit:
+    // tensor copies of planes never published, then (bounded) the last min(issued, ns)
+    // planes, the only ones that may still be in flight (in normal runs the consumers wait
+    // for them anyway).
+    cp_async_wait<0>();
+    for (int j = 0, s2 = pslot; j < unpub; ++j, s2 = (s2 + 1 == ns) ? 0 : s2 + 1)
+        mbar_wait_bounded(g.tma_u32 + 8u * s2, (tbits >> s2) & 1u, 100000000ull);
+    for (int k = 0; k < min(issued, ns); ++k) {
+        if (--pos.slot < 0) {
+            pos.slot = ns - 1;
+            pos.phase ^= 1u;
+        }
+        mbar_wait_bounded(g.full_u32 + 8u * pos.slot, pos.phase, 100000000ull);
+    }
+}
+
+}  // namespace gst

@@ -2,29 +2,30 @@
 // Sec. 2.1) for star, box and diamond offset sets of radius R on a 2D or 3D grid.
 //
 // Design (sm_103a):
-//  * A CTA owns an output tile of TX x TY cells (TX = 128, TY = blockDim.y * VY) and walks a
-//    range of z-planes from low to high z (a range may continue into the next tile column).
-//  * Input planes (tile plus an R-row halo in y and one 16-byte chunk of halo in x) land in a
-//    ring of NSTAGE shared-memory slots, each with an mbarrier.  When rows are 16-byte
-//    aligned one thread issues a 3D TMA tensor copy per plane (the hardware zero-fills
-//    everything outside the grid: the Dirichlet ghosts); for a periodic grid the few chunks
-//    of an edge tile that wrap are read into registers one plane ahead and stored over the
-//    zero fill once the copy has landed.  Otherwise 16-byte cp.async (or, for odd row
-//    lengths, element loads) fill the slot.  Plane z+NSTAGE-1 is in flight while plane z is
-//    consumed; every wait is bounded by %globaltimer.
+//  * A CTA owns an output tile of TX x TY cells (TX = 128, TY = by * VY) and walks a range of
+//    z-planes from low to high z (a range may continue into the next tile column).
+//  * Warp specialisation (ring.cuh): by rows of consumer threads compute while one extra
+//    producer warp keeps a ring of `nstage` shared-memory slots (a launch parameter, sized by
+//    the host to fill the shared memory the resident CTAs leave) filled with input planes --
+//    tile plus an R-row halo in y and one 16-byte chunk of halo in x -- by 3D TMA tensor
+//    copies (hardware zero fill = Dirichlet ghosts; the chunks a periodic grid wraps into an
+//    edge tile are patched over the fill once the copy has landed).  Slots are handed over by
+//    "full"/"empty" mbarriers, never by a CTA-wide barrier; every wait is bounded.
 //  * Each plane contributes to the 2R+1 output planes it touches: every thread keeps, per owned
 //    cell, a queue of 2R+1 FP32 partial sums in registers, adds the 2D slice of the offset set
 //    that lies at each dz, and writes the oldest sum once the plane R above it has arrived.
 //    A star therefore reads its z-neighbours from registers and only the in-plane cross from
 //    shared memory; a box or diamond reuses every shared-memory read for 2R+1 outputs.
 //  * In-plane neighbours come from shared memory as 16-byte vectors: a thread's VX cells are
-//    contiguous in x, so one row of its window (VX + 2m values) is a few aligned loads.
-//  * 2D grids use the same kernel with no z-radius (one plane per CTA).
+//    contiguous in x, so one row of its window (VX + 2m values) is a few aligned loads, and
+//    pairs of cells share the packed two-lane FP32 FMA.
+//  * 2D grids use the same kernel with no z-radius (one plane per piece).
 #pragma once
 
 #include <utility>
 
 #include "common.cuh"
+#include "ring.cuh"
 
 namespace gst {
 
@@ -49,6 +50,26 @@ template <int P, typename F> __device__ __forceinline__ void phase_switch(int ph
         GST_PHASE_CASE(8)
 #undef GST_PHASE_CASE
     default: break;
+    }
+}
+
+// a[v] = fma(c, w[v], a[v]) for v < N.  PAIRED issues the packed two-lane FP32 FMA of sm_100+
+// on (v, v+1) -- each lane rounds exactly like fmaf -- which halves the FMA instructions when
+// w[v], w[v+1] come from one aligned 8-byte pair of a vector load (an even x offset).
+template <int N, bool PAIRED>
+__device__ __forceinline__ void fma_n(float c, const float *w, float *a) {
+    if constexpr (PAIRED && N % 2 == 0) {
+        const float2 c2 = make_float2(c, c);
+#pragma unroll
+        for (int v = 0; v < N; v += 2) {
+            const float2 r =
+                __ffma2_rn(c2, make_float2(w[v], w[v + 1]), make_float2(a[v], a[v + 1]));
+            a[v] = r.x;
+            a[v + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < N; ++v) a[v] = fmaf(c, w[v], a[v]);
     }
 }
 
@@ -125,7 +146,44 @@ template <typename T> struct StreamParams {
     int tiles_x, tiles_y;
     int work;           // planes per CTA (flattened tile x z sequence)
     int use_tma;        // 1 = tensor-map loads (tmap describes `in`)
+    int nstage;         // ring slots, 2 .. kMaxStages
     int *err;           // device error word (may be null)
+};
+
+// What happens to a finished output row segment (VY rows of VX cells at (zo, oy, ox)): the
+// plain sweep stores it; fused operators (the wave update) supply their own epilogue with
+// their own parameter block.
+// An epilogue may also read operands of its own: `prefetch` is called for output plane zo at
+// the top of the iteration that finishes it (before the ring wait and the stencil), so that
+// the loads it issues into `Regs` overlap them; `apply` then consumes the registers.
+struct PlainStoreEpi {
+    struct Params {};
+    template <int VY, int VX> struct Regs {};
+    template <typename T, int VY, int VX>
+    __device__ __forceinline__ static void prefetch(const StreamParams<T> &, const Params &, int,
+                                                    int, int, bool, int, Regs<VY, VX> &) {}
+    template <typename T, int VY, int VX>
+    __device__ __forceinline__ static void apply(const StreamParams<T> &p, const Params &, int zo,
+                                                 int oy, int ox, bool xfull, int vy_valid,
+                                                 const Regs<VY, VX> &,
+                                                 const float (&vals)[VY][VX]) {
+        T *orow = p.out + ((size_t)zo * p.ny + oy) * p.nx + ox;
+#pragma unroll
+        for (int vy = 0; vy < VY; ++vy) {
+            if (vy >= vy_valid) break;
+            T *dst = orow + (size_t)vy * p.nx;
+            if (xfull) {
+                T tmp[VX];
+#pragma unroll
+                for (int vx = 0; vx < VX; ++vx) tmp[vx] = Storage<T>::from_float(vals[vy][vx]);
+                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tmp);
+            } else {
+#pragma unroll
+                for (int vx = 0; vx < VX; ++vx)
+                    if (ox + vx < p.nx) dst[vx] = Storage<T>::from_float(vals[vy][vx]);
+            }
+        }
+    }
 };
 
 // How the partial-sum queue is indexed:
@@ -135,7 +193,7 @@ template <typename T> struct StreamParams {
 //                   the plane's phase adds it and the 2R single-point z terms to the queue.
 enum QueueMode : int { kQueueUnrolled = 0, kQueueRotate = 1, kQueueStarSplit = 2 };
 
-template <typename T, int NDIM, int SHAPE, int R, int VY, int NSTAGE, int QMODE>
+template <typename T, int NDIM, int SHAPE, int R, int VY, int QMODE>
 struct StreamKernel {
     static constexpr int RZ = (NDIM == 3) ? R : 0;
     static constexpr int P = 2 * RZ + 1;
@@ -147,11 +205,10 @@ struct StreamKernel {
     using OT = OffsetTable<NDIM, SHAPE, R>;
     static constexpr int NPTS = OT::count;
     static constexpr bool CREG = NPTS <= 32;         // coefficients held in registers
-    // Wide-halo 3D stars with one row per thread may run 512-thread CTAs (taller tiles, less
-    // halo per output row); everything else is limited to 256 threads.
-    static constexpr int MAX_THREADS = (NDIM == 3 && SHAPE == kStar && R >= 3 && VY == 1) ? 512 : 256;
-    static constexpr int KMAX = 4;                   // cp.async chunks held in registers
-    static constexpr int KP = 2;                     // TMA patch chunks per thread
+    // Consumer threads per CTA: with the producer warp a CTA is then at most 8 (16) warps,
+    // two (four) per SM sub-partition, which keeps the register cap at 255 (128).  Wide-halo
+    // 3D stars with one row per thread may take the taller tiles.
+    static constexpr int MAX_THREADS = (NDIM == 3 && SHAPE == kStar && R >= 3 && VY == 1) ? 480 : 224;
     static_assert(R <= A, "x halo must fit in one 16-byte chunk");
     static_assert(QMODE != kQueueStarSplit || SHAPE == kStar, "split mode is for stars");
 
@@ -167,50 +224,60 @@ struct StreamKernel {
         return m;
     }
 
-    // ring slot size (rounded to 128 bytes) and the shared memory of a CTA: NSTAGE slots
-    // followed by one mbarrier per slot
+    // ring slot size (one field, rounded to 128 bytes) and the shared memory of a CTA
     __host__ __device__ static constexpr size_t slot_bytes(int by) {
-        return ((size_t)PITCH * (by * VY + 2 * R) * sizeof(T) + 127) / 128 * 128;
+        return RingLayout::field_size(PITCH, by * VY + 2 * R, (int)sizeof(T));
     }
-    static size_t smem_bytes(int by) { return NSTAGE * slot_bytes(by) + NSTAGE * 8; }
+    static size_t smem_bytes(int by, int nstage) {
+        return RingLayout::bytes((uint32_t)slot_bytes(by), nstage);
+    }
 };
 
-template <typename T, int NDIM, int SHAPE, int R, int VY, int NSTAGE, int QMODE>
+template <typename T, int NDIM, int SHAPE, int R, int VY, int QMODE, class EPI = PlainStoreEpi>
 __global__ void __launch_bounds__(
-    (StreamKernel<T, NDIM, SHAPE, R, VY, NSTAGE, QMODE>::MAX_THREADS))
+    (StreamKernel<T, NDIM, SHAPE, R, VY, QMODE>::MAX_THREADS) + 32)
     stream_sweep_kernel(const __grid_constant__ StreamParams<T> p,
-                        const __grid_constant__ ConstCoeffs<OffsetTable<NDIM, SHAPE, R>::count> cf) {
-    using K = StreamKernel<T, NDIM, SHAPE, R, VY, NSTAGE, QMODE>;
+                        const __grid_constant__ ConstCoeffs<OffsetTable<NDIM, SHAPE, R>::count> cf,
+                        const __grid_constant__ typename EPI::Params ep) {
+    using K = StreamKernel<T, NDIM, SHAPE, R, VY, QMODE>;
     constexpr int RZ = K::RZ, P = K::P, A = K::A, VX = K::VX, PITCH = K::PITCH, TX = K::TX;
-    constexpr int ES = (int)sizeof(T);
-
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *smem = reinterpret_cast<T *>(smem_raw);
 
-    const int by = blockDim.y;
+    // blockDim = (BX, by + 32 / BX): by rows of consumer threads, then one producer warp
+    const int by = (int)blockDim.y - 32 / K::BX;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * K::BX + tx, nthr = K::BX * by;
+    const int tid = ty * K::BX + tx;
+    const int ncons = K::BX * by;  // consumer threads (whole warps)
+    const int lane = tid & 31;
     const int TY = by * VY;
     const int rows = TY + 2 * R;
-    const size_t slot_bytes = K::slot_bytes(by);
-    const uint32_t bar_u32 =
-        static_cast<uint32_t>(__cvta_generic_to_shared(smem_raw)) + (uint32_t)(NSTAGE * slot_bytes);
-    constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bounded waits: 2 s
-    // loader mode: 2 = TMA tensor copies, 1 = 16-byte cp.async, 0 = scalar rows
-    const int mode = p.use_tma ? 2 : (p.aligned ? 1 : 0);
-    if (tid == 0) {
-        const uint32_t arrivals = mode == 2 ? 1u : (uint32_t)nthr;
-        for (int i = 0; i < NSTAGE; ++i) mbar_init(bar_u32 + 8u * i, arrivals);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    uint32_t phase_bits = 0;  // parity of the next phase of every slot's mbarrier
-    bool failed = false;
+    Ring g;
+    g.setup(smem_raw, (uint32_t)K::slot_bytes(by), 1, p.nstage);
+    if (tid == 0) g.init(ncons / 32);
+    __syncthreads();  // the only CTA-wide barrier: from here on the warps meet at mbarriers
 
     const int nx = p.nx, ny = p.ny;
-    const bool periodic = p.periodic != 0;
     const bool aligned = p.aligned != 0;
-    const size_t plane_stride = (size_t)nx * ny;
+    RingWork wk;
+    wk.setup(p.tiles_x, p.tiles_y, NDIM == 3 ? p.nz : 1, p.work, TX, TY, RZ);
+
+    if (tid >= ncons) {
+        // producer warp
+        RingSource<T, 1> src;
+        src.tmap = &p.tmap;
+        src.field = &p.in;
+        src.nx = nx;
+        src.ny = ny;
+        src.nz = p.nz;
+        src.periodic = p.periodic != 0;
+        src.aligned = aligned;
+        src.use_tma = p.use_tma != 0;
+        src.rows = rows;
+        ring_produce<T, 1, NDIM, R, A, PITCH, TX>(g, src, wk, p.err, lane);
+        return;
+    }
+
+    // ---- consumer warps ---------------------------------------------------------------
     // coefficients: registers for small stencils, the parameter bank otherwise
     float creg[K::CREG ? K::NPTS : 1];
     if constexpr (K::CREG) {
@@ -222,167 +289,28 @@ __global__ void __launch_bounds__(
         if constexpr (K::CREG) return creg[idx];
         else return cf.c[idx];
     };
+    const int thr_off = (ty * VY) * PITCH + A + tx * VX;  // element offset of the thread's base
+    bool failed = false;
 
-    // Persistent, balanced work: this CTA owns planes [w, w_end) of the flattened
-    // (tile, z) sequence, possibly spanning the end of one tile column and the start of the
-    // next; each piece is one z-stream with its own prologue.
-    const int nzp = NDIM == 3 ? p.nz : 1;
-    const long long total = (long long)p.tiles_x * p.tiles_y * nzp;
-    long long w = (long long)blockIdx.x * p.work;
-    const long long w_end = min(total, w + (long long)p.work);
-    while (w < w_end) {
-        const int tile = (int)(w / nzp);
-        const int z_begin = (int)(w % nzp);
-        const int z_end = (int)min((long long)nzp, (long long)z_begin + (w_end - w));
-        w += z_end - z_begin;
-        const int tix = tile % p.tiles_x, tiy = tile / p.tiles_x;
-        const int x0 = tix * TX, y0 = tiy * TY;
-        const int zs = z_begin - RZ, zl = z_end + RZ;
-
-        const uint32_t smem_u32 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
-        // ---- loader state for this tile -------------------------------------------------
-        // chunk c of the row-major tile (row c / CPR, 16-byte chunk c % CPR) lives at byte 16c
-        // of its ring slot
-        constexpr int CPR = PITCH / A;
-        const int nchunks = CPR * rows;
-        const int oob_lo_row = max(0, R - y0);                       // rows above the grid
-        const int oob_hi_row = min(rows, max(0, ny - (y0 - R)));     // first row below the grid
-        const int oob_lo_chk = max(0, (A - x0 + A - 1) / A);          // chunks left of the grid
-        const int oob_hi_chk = min(CPR, max(0, (nx - (x0 - A) + A - 1) / A));
-        // cp.async mode: up to KMAX chunks per thread with precomputed addresses
-        uint32_t ld_dst[K::KMAX];
-        int ld_src[K::KMAX];
-        int nk = 0;
-        // TMA mode: chunks the tensor copy zero-filled but a periodic grid wraps ("patches"),
-        // up to KP per thread, loaded into registers one plane ahead
-        uint32_t pt_dst[K::KP];
-        int pt_src[K::KP];
-        int npt = 0;
-        if (mode == 1) {
-    #pragma unroll
-            for (int k = 0; k < K::KMAX; ++k) {
-                const int c = tid + k * nthr;
-                ld_dst[k] = 0;
-                ld_src[k] = -1;
-                if (c < nchunks) {
-                    const int row = c / CPR, cc = c - row * CPR;
-                    bool ok = true;
-                    const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
-                    const int gx = wrap_or_flag(x0 - A + cc * A, nx, periodic, ok);
-                    ld_dst[k] = (uint32_t)(c * 16);
-                    ld_src[k] = ok ? gy * nx + gx : -1;
-                    nk = k + 1;
-                }
-            }
-        } else if (mode == 2 && periodic) {
-            // patch list: every chunk of the out-of-grid rows, then the out-of-grid chunks of
-            // the in-grid rows; patch i goes to thread i mod nthr
-            const int nrow_oob = oob_lo_row + (rows - oob_hi_row);
-            const int nin_rows = oob_hi_row - oob_lo_row;
-            const int nchk_oob = oob_lo_chk + (CPR - oob_hi_chk);
-            const int npatch = nrow_oob * CPR + nin_rows * nchk_oob;
-    #pragma unroll
-            for (int k = 0; k < K::KP; ++k) {
-                const int i = tid + k * nthr;
-                pt_dst[k] = 0;
-                pt_src[k] = 0;
-                if (i < npatch) {
-                    int row, cc;
-                    if (i < nrow_oob * CPR) {
-                        const int q = i / CPR;
-                        row = q < oob_lo_row ? q : oob_hi_row + (q - oob_lo_row);
-                        cc = i - q * CPR;
-                    } else {
-                        const int j = i - nrow_oob * CPR;
-                        const int q = j / nchk_oob, e = j - q * nchk_oob;
-                        row = oob_lo_row + q;
-                        cc = e < oob_lo_chk ? e : oob_hi_chk + (e - oob_lo_chk);
-                    }
-                    bool ok = true;
-                    const int gy = wrap_or_flag(y0 - R + row, ny, true, ok);
-                    const int gx = wrap_or_flag(x0 - A + cc * A, nx, true, ok);
-                    pt_dst[k] = (uint32_t)((row * CPR + cc) * 16);
-                    pt_src[k] = gy * nx + gx;
-                    npt = k + 1;
-                }
-            }
+    RingPos pos;  // ring position of the next plane
+    // wait for the next plane to land; null once a bounded wait has given up
+    auto begin_plane = [&]() -> const T * {
+        if (!g.wait_full(pos.slot, pos.phase)) {
+            failed = true;  // the whole warp
+            return nullptr;
         }
-        uint4 pt_val[K::KP];
+        return reinterpret_cast<const T *>(g.slot_ptr(pos.slot)) + thr_off;
+    };
+    // this warp has read the slot: release it to the producer and move on
+    auto end_plane = [&]() {
+        g.release(pos.slot, lane);
+        pos.advance(g.ns);
+    };
 
-        // Fill ring slot `slot` with input plane zi.
-        //  mode 2 (TMA): thread 0 announces the box bytes and issues one 3D tensor copy; the
-        //    hardware zero-fills everything outside the grid (Dirichlet ghosts); periodic
-        //    edge tiles overwrite the wrapped chunks from registers (patch_plane).
-        //  mode 1 (cp.async): every thread copies its 16-byte chunks, zero-filling ghosts,
-        //    and its arrival on the slot's mbarrier fires when its copies have landed.
-        //  mode 0 (scalar rows): element loads and stores, then an arrival.
-        auto load_plane = [&](int zi, int slot) {
-            bool zok = true;
-            const int gz = (NDIM == 3) ? wrap_or_flag(zi, p.nz, periodic, zok) : 0;
-            const uint32_t bar = bar_u32 + 8u * (uint32_t)slot;
-            const uint32_t sbase = smem_u32 + (uint32_t)(slot * slot_bytes);
-            if (mode == 2) {
-                if (tid == 0) {
-                    fence_proxy_async_shared();  // earlier reads of this slot come first
-                    mbar_arrive_expect_tx(bar, (uint32_t)(PITCH * rows * ES));
-                    const int zc = (NDIM == 3) ? (periodic ? gz : zi) : 0;
-                    tma_load_3d(sbase, &p.tmap, x0 - A, y0 - R, zc, bar);
-                }
-                return;
-            }
-            const T *plane = p.in + (size_t)gz * plane_stride;
-            if (mode == 1) {
-    #pragma unroll
-                for (int k = 0; k < K::KMAX; ++k) {
-                    if (k < nk) {
-                        const bool ok = zok && ld_src[k] >= 0;
-                        const T *src = ok ? plane + ld_src[k] : p.in;
-                        cp_async16_u32(sbase + ld_dst[k], src, ok ? 16 : 0);
-                    }
-                }
-                for (int c = tid + K::KMAX * nthr; c < nchunks; c += nthr) {
-                    const int row = c / CPR, cc = c - row * CPR;
-                    bool ok = zok;
-                    const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
-                    const int gx = wrap_or_flag(x0 - A + cc * A, nx, periodic, ok);
-                    const T *src = ok ? plane + gy * nx + gx : p.in;
-                    cp_async16_u32(sbase + (uint32_t)(c * 16), src, ok ? 16 : 0);
-                }
-                cp_async_mbar_arrive_noinc(bar);
-                return;
-            }
-            // scalar path: only the cells the stencil reads (x0-R .. x0+TX+R)
-            T *dst = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(smem) +
-                                           (size_t)slot * slot_bytes);
-            const int wcols = TX + 2 * R;
-            const int n = wcols * rows;
-            for (int e = tid; e < n; e += nthr) {
-                const int row = e / wcols, col = e - row * wcols;
-                bool ok = zok;
-                const int gy = wrap_or_flag(y0 - R + row, ny, periodic, ok);
-                const int gx = wrap_or_flag(x0 - R + col, nx, periodic, ok);
-                const T v = ok ? plane[(size_t)gy * nx + gx] : Storage<T>::from_float(0.0f);
-                dst[row * PITCH + (A - R) + col] = v;
-            }
-            mbar_arrive(bar);
-        };
-        // patches of plane zi into registers (TMA mode, periodic edge tiles)
-        auto fetch_patches = [&](int zi) {
-            if (npt == 0) return;
-            bool zok = true;
-            const int gz = (NDIM == 3) ? wrap_or_flag(zi, p.nz, true, zok) : 0;
-            const T *plane = p.in + (size_t)gz * plane_stride;
-    #pragma unroll
-            for (int k = 0; k < K::KP; ++k)
-                if (k < npt) pt_val[k] = __ldg(reinterpret_cast<const uint4 *>(plane + pt_src[k]));
-        };
-        auto store_patches = [&](int slot) {
-            if (npt == 0) return;
-            unsigned char *base = reinterpret_cast<unsigned char *>(smem) + (size_t)slot * slot_bytes;
-    #pragma unroll
-            for (int k = 0; k < K::KP; ++k)
-                if (k < npt) *reinterpret_cast<uint4 *>(base + pt_dst[k]) = pt_val[k];
-        };
+    for (long long w = wk.w_first; w < wk.w_end && !failed;) {
+        const RingPiece q = wk.piece_at(w);
+        w += q.z_end - q.z_begin;
+        const int z_begin = q.z_begin, z_end = q.z_end, zl = q.zl;
 
         float acc[P][VY][VX];
     #pragma unroll
@@ -392,38 +320,20 @@ __global__ void __launch_bounds__(
     #pragma unroll
                 for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] = 0.0f;
 
-        // prologue: planes zs .. zs+NSTAGE-2 in flight
-    #pragma unroll
-        for (int k = 0; k < NSTAGE - 1; ++k)
-            if (zs + k < zl) load_plane(zs + k, k);
-        fetch_patches(zs);
-
         // output addressing, hoisted
-        const int ox = x0 + tx * VX;
-        const int oy = y0 + ty * VY;
-        T *const obase = p.out + (size_t)oy * nx + ox;
+        const int ox = q.x0 + tx * VX;
+        const int oy = q.y0 + ty * VY;
         const bool xfull = aligned && (ox + VX <= nx);
         const int vy_valid = min(VY, ny - oy);  // may be <= 0
-        const int thr_off = (ty * VY) * PITCH + A + tx * VX;  // element offset of the thread's base
 
+        typename EPI::template Regs<VY, VX> eregs;
+        auto prefetch_output = [&](int zo) {
+            if (zo < z_begin || zo >= z_end) return;
+            EPI::template prefetch<T, VY, VX>(p, ep, zo, oy, ox, xfull, vy_valid, eregs);
+        };
         auto store_output = [&](int zo, const float (&vals)[VY][VX]) {
             if (zo < z_begin || zo >= z_end) return;
-            T *orow = obase + (size_t)zo * plane_stride;
-    #pragma unroll
-            for (int vy = 0; vy < VY; ++vy) {
-                if (vy >= vy_valid) break;
-                T *dst = orow + (size_t)vy * nx;
-                if (xfull) {
-                    T tmp[VX];
-    #pragma unroll
-                    for (int vx = 0; vx < VX; ++vx) tmp[vx] = Storage<T>::from_float(vals[vy][vx]);
-                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(tmp);
-                } else {
-    #pragma unroll
-                    for (int vx = 0; vx < VX; ++vx)
-                        if (ox + vx < nx) dst[vx] = Storage<T>::from_float(vals[vy][vx]);
-                }
-            }
+            EPI::template apply<T, VY, VX>(p, ep, zo, oy, ox, xfull, vy_valid, eregs, vals);
         };
 
         // add the in-plane slice(s) of the plane at `tb` to the queue; JOF(dz) = queue index of
@@ -450,11 +360,8 @@ __global__ void __launch_bounds__(
                                         constexpr int idx = K::OT::index(dz, dy, dx);
                                         if constexpr (idx >= 0) {
                                             const float c = coef(std::integral_constant<int, idx>{});
-    #pragma unroll
-                                            for (int vx = 0; vx < VX; ++vx) {
-                                                float &dst = IPO ? tmp[vy][vx] : acc[j][vy][vx];
-                                                dst = fmaf(c, win[vx + dx + R], dst);
-                                            }
+                                            float *dst = IPO ? tmp[vy] : acc[j][vy];
+                                            fma_n<VX, dx % 2 == 0>(c, win + (dx + R), dst);
                                         }
                                     });
                                 }
@@ -472,28 +379,8 @@ __global__ void __launch_bounds__(
                 for (int vx = 0; vx < VX; ++vx) a[vy][vx] = 0.0f;
         };
 
-        // one plane: wait for it, keep the ring full, consume it
-        auto begin_plane = [&](int zi, int slot) -> const T * {
-            const bool ok = mbar_wait_bounded(bar_u32 + 8u * (uint32_t)slot,
-                                              (phase_bits >> slot) & 1u, kWaitLimitNs);
-            phase_bits ^= 1u << slot;
-            if (ok) store_patches(slot);  // after the tensor copy of this plane has landed
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                return nullptr;
-            }
-            const int zn = zi + NSTAGE - 1;
-            int sn = slot + NSTAGE - 1;
-            if (sn >= NSTAGE) sn -= NSTAGE;
-            if (zn < zl) load_plane(zn, sn);
-            if (zi + 1 < zl) fetch_patches(zi + 1);
-            return reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(smem) +
-                                               (size_t)slot * slot_bytes) +
-                   thr_off;
-        };
 
-        int zi = zs;
-        int slot = 0;
+        int zi = q.zs;
         float dummy[VY][VX];
         if constexpr (QMODE == kQueueUnrolled) {
             bool done = false;
@@ -505,7 +392,8 @@ __global__ void __launch_bounds__(
                         done = true;
                         return;
                     }
-                    const T *tb = begin_plane(zi, slot);
+                    prefetch_output(zi - RZ);
+                    const T *tb = begin_plane();
                     if (!tb) {
                         done = true;
                         return;
@@ -514,21 +402,23 @@ __global__ void __launch_bounds__(
                         constexpr int dz = decltype(dz_c)::value;
                         return std::integral_constant<int, imod_c(ph - dz, P)>{};
                     }, std::false_type{}, dummy);
+                    end_plane();
                     constexpr int jo = imod_c(ph - RZ, P);
                     store_output(zi - RZ, acc[jo]);
                     zero_slot(acc[jo]);
                     ++zi;
-                    slot = (slot + 1 == NSTAGE) ? 0 : slot + 1;
                 });
             }
         } else if constexpr (QMODE == kQueueRotate) {
             for (; zi < zl; ++zi) {
-                const T *tb = begin_plane(zi, slot);
+                prefetch_output(zi - RZ);
+                const T *tb = begin_plane();
                 if (!tb) break;
                 accumulate(tb, [](auto dz_c) {
                     constexpr int dz = decltype(dz_c)::value;
                     return std::integral_constant<int, RZ - dz>{};
                 }, std::false_type{}, dummy);
+                end_plane();
                 store_output(zi - RZ, acc[0]);
     #pragma unroll
                 for (int j = 0; j + 1 < P; ++j)
@@ -537,13 +427,13 @@ __global__ void __launch_bounds__(
     #pragma unroll
                         for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] = acc[j + 1][vy][vx];
                 zero_slot(acc[P - 1]);
-                slot = (slot + 1 == NSTAGE) ? 0 : slot + 1;
             }
         } else {
             // star split: in-plane cross into tmp, then a phase switch for the z line
             int ph = 0;
             for (; zi < zl; ++zi) {
-                const T *tb = begin_plane(zi, slot);
+                prefetch_output(zi - RZ);
+                const T *tb = begin_plane();
                 if (!tb) break;
                 float tmp[VY][VX];
                 zero_slot(tmp);
@@ -553,45 +443,40 @@ __global__ void __launch_bounds__(
                 float ctr[VY][VX];
     #pragma unroll
                 for (int vy = 0; vy < VY; ++vy) {
-                    float w[VX];
-                    load_span<T, 0, VX, 0>(tb + (vy + R) * PITCH, w);
+                    float wv[VX];
+                    load_span<T, 0, VX, 0>(tb + (vy + R) * PITCH, wv);
     #pragma unroll
-                    for (int vx = 0; vx < VX; ++vx) ctr[vy][vx] = w[vx];
+                    for (int vx = 0; vx < VX; ++vx) ctr[vy][vx] = wv[vx];
                 }
+                end_plane();
                 phase_switch<P>(ph, [&](auto ph_c) {
                     constexpr int PH = decltype(ph_c)::value;
                     static_for<P>([&](auto dzi_c) {
                         constexpr int dz = decltype(dzi_c)::value - RZ;
                         constexpr int j = imod_c(PH - dz, P);
     #pragma unroll
-                        for (int vy = 0; vy < VY; ++vy)
+                        for (int vy = 0; vy < VY; ++vy) {
+                            if constexpr (dz == 0) {
     #pragma unroll
-                            for (int vx = 0; vx < VX; ++vx) {
-                                if constexpr (dz == 0)
-                                    acc[j][vy][vx] += tmp[vy][vx];
-                                else
-                                    acc[j][vy][vx] = fmaf(
-                                        coef(std::integral_constant<int, K::OT::index(dz, 0, 0)>{}),
-                                        ctr[vy][vx], acc[j][vy][vx]);
+                                for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] += tmp[vy][vx];
+                            } else {
+                                fma_n<VX, true>(
+                                    coef(std::integral_constant<int, K::OT::index(dz, 0, 0)>{}),
+                                    ctr[vy], acc[j][vy]);
                             }
+                        }
                     });
                     constexpr int jo = imod_c(PH - RZ, P);
                     store_output(zi - RZ, acc[jo]);
                     zero_slot(acc[jo]);
                 });
                 ph = (ph + 1 == P) ? 0 : ph + 1;
-                slot = (slot + 1 == NSTAGE) ? 0 : slot + 1;
             }
         }
-        if (failed) {
-            // a bounded wait expired: report, let copies still in flight land, and stop
-            if (tid == 0) latch_error(p.err, kErrTimeout);
-            for (int i = 0; i < NSTAGE; ++i)
-                mbar_wait_bounded(bar_u32 + 8u * i, (phase_bits >> i) & 1u, 100000000ull);
-            return;
-        }
-        __syncthreads();  // the ring is reused by the next piece
-    }  // while (w < w_end)
+    }  // pieces
+    // a bounded wait gave up: report and stop (the producer lets the copies in flight land
+    // before the CTA exits)
+    if (failed) g.fail(p.err, lane);
 }
 
 }  // namespace gst

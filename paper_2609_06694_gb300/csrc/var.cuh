@@ -5,14 +5,19 @@
 //                                                      at the shifted cell)
 //   div(k grad u), unit spacing, conservative star-1 form with face k = mean of the two cells.
 //
-// Design: a CTA owns a 128-cell x TY tile and walks z.  The 2R+1 input planes an output plane
-// needs (plus one in flight) sit in a ring of shared-memory slots filled by 16-byte cp.async
-// (zero fill = Dirichlet ghosts, wrapped addresses = periodic), so each output is computed
-// in one pass with a single FP32 accumulator; coefficient arrays are read straight from
-// global memory (each value is used once, so staging would not save traffic).
+// Design: a CTA owns a 128-cell x TY tile and walks z, one output plane at a time with a
+// single FP32 accumulator per cell.
+//  * general VAR sweeps: the 2R+1 input planes an output plane needs (plus one in flight) sit
+//    in a ring of shared-memory slots filled by all threads with 16-byte cp.async (zero fill
+//    = Dirichlet ghosts, wrapped addresses = periodic); coefficient arrays are read straight
+//    from global memory (each value is used once, so staging would not save traffic).
+//  * div(k grad u): the warp-specialised plane ring of ring.cuh (a producer warp
+//    tensor-copies the u and k tiles of each plane into one slot); consumer warps hold the
+//    window z-1, z, z+1 and release plane z-1 once output z is computed.
 #pragma once
 
 #include "common.cuh"
+#include "ring.cuh"
 #include "stream.cuh"
 
 namespace gst {
@@ -270,126 +275,182 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------------------
-// div(k grad u)
+// div(k grad u) on the plane ring (ring.cuh): the producer warp tensor-copies the u and k
+// tiles of each plane into one slot (two fields); every consumer warp holds a window of the
+// 2RZ+1 planes z-1, z, z+1, writes output plane z and releases plane z-1.
 // ---------------------------------------------------------------------------------------
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) divkgrad_kernel(const __grid_constant__ VarParams<T> p) {
-    constexpr int VX = 16 / (int)sizeof(T), A = VX, TX = 128, BX = TX / VX, R = 1;
-    constexpr int PITCH = TX + 2 * A;
-    constexpr int RZ = NDIM == 3 ? 1 : 0;
-    constexpr int NSLOT = 2 * RZ + 2;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *su = reinterpret_cast<T *>(smem_raw);
-    const int by = blockDim.y, tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * BX + tx, nthr = BX * by;
-    const int TY = by;
-    const int rows = TY + 2 * R;
-    const int plane_elems = PITCH * rows;
-    T *sk = su + NSLOT * plane_elems;
-    int b = blockIdx.x;
-    const int tix = b % p.tiles_x;
-    b /= p.tiles_x;
-    const int tiy = b % p.tiles_y, tiz = b / p.tiles_y;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int x0 = tix * TX, y0 = tiy * TY;
-    const int z_begin = NDIM == 3 ? tiz * p.zchunk : 0;
-    const int z_end = NDIM == 3 ? min(nz, z_begin + p.zchunk) : 1;
-    const bool periodic = p.periodic != 0, aligned = p.aligned != 0;
-    const size_t pstride = (size_t)nx * ny;
-    const int ox = x0 + tx * VX, oy = y0 + ty;
-    const bool vec = aligned && ox + VX <= nx;
-    const int nvalid = nx - ox;
-    const T *kfield = p.w[0];
+template <typename T> struct DivkParams {
+    CUtensorMap tmap[2];  // u, k (valid when use_tma)
+    const T *field[2];    // u, k
+    T *out;
+    int nx, ny, nz;
+    int periodic, aligned, use_tma;
+    int tiles_x, tiles_y, work, nstage;
+    int *err;
+};
 
-    auto slot_of = [&](int zi) { return ((zi - z_begin + RZ) % NSLOT + NSLOT) % NSLOT; };
-    TileLoader<T, R, A, PITCH> loader;
-    loader.init(x0, y0, rows, nx, ny, nz, periodic, aligned, NDIM == 3, tid, nthr);
-    auto load = [&](int zi) {
-        const int s = slot_of(zi);
-        loader.load(p.in, su + s * plane_elems, zi);
-        loader.load(kfield, sk + s * plane_elems, zi);
-    };
-    for (int zi = z_begin - RZ; zi <= z_begin + RZ; ++zi) {
-        load(zi);
-        cp_async_commit();
+template <typename T, int NDIM> struct DivkKernel {
+    static constexpr int VX = 16 / (int)sizeof(T), A = VX, TX = 128, BX = TX / VX, R = 1;
+    static constexpr int PITCH = TX + 2 * A;
+    static constexpr int RZ = NDIM == 3 ? 1 : 0;
+    static constexpr int MAX_THREADS = 224;  // consumers; the CTA adds the producer warp
+    __host__ __device__ static constexpr uint32_t field_bytes(int by) {
+        return RingLayout::field_size(PITCH, by + 2 * R, (int)sizeof(T));
     }
-    const int off = (ty + R) * PITCH + A + tx * VX;  // the thread's first cell in a slot
-    for (int zo = z_begin; zo < z_end; ++zo) {
-        if (zo + RZ + 1 < z_end + RZ) load(zo + RZ + 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        if (oy < ny && ox < nx) {
-            const int s0 = slot_of(zo) * plane_elems + off;
-            float u0[VX + 2], k0[VX + 2];  // centre row with one cell each side
-            load_span<T, -1, VX + 1, -1>(su + s0, u0);
-            load_span<T, -1, VX + 1, -1>(sk + s0, k0);
+    static size_t smem_bytes(int by, int nstage) {
+        return RingLayout::bytes(2 * field_bytes(by), nstage);
+    }
+};
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(DivkKernel<T, NDIM>::MAX_THREADS + 32)
+    divkgrad_kernel(const __grid_constant__ DivkParams<T> p) {
+    using K = DivkKernel<T, NDIM>;
+    constexpr int VX = K::VX, A = K::A, TX = K::TX, BX = K::BX, R = 1, PITCH = K::PITCH;
+    constexpr int RZ = K::RZ;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // blockDim = (BX, by + 32 / BX): by rows of consumer threads (one output row each), then
+    // the producer warp
+    const int by = (int)blockDim.y - 32 / BX;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * BX + tx, ncons = BX * by, lane = tid & 31;
+    const int TY = by, rows = TY + 2 * R;
+    Ring g;
+    g.setup(smem_raw, K::field_bytes(by), 2, p.nstage);
+    if (tid == 0) g.init(ncons / 32);
+    __syncthreads();  // the only CTA-wide barrier
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const bool periodic = p.periodic != 0, aligned = p.aligned != 0;
+    RingWork wk;
+    wk.setup(p.tiles_x, p.tiles_y, NDIM == 3 ? nz : 1, p.work, TX, TY, RZ);
+
+    if (tid >= ncons) {
+        RingSource<T, 2> src;
+        src.tmap = p.tmap;
+        src.field = p.field;
+        src.nx = nx;
+        src.ny = ny;
+        src.nz = nz;
+        src.periodic = periodic;
+        src.aligned = aligned;
+        src.use_tma = p.use_tma != 0;
+        src.rows = rows;
+        ring_produce<T, 2, NDIM, R, A, PITCH, TX>(g, src, wk, p.err, lane);
+        return;
+    }
+
+    const size_t pstride = (size_t)nx * ny;
+    const int off = (ty + R) * PITCH + A + tx * VX;  // the thread's first cell in a field
+    const uint32_t kofs = g.field_bytes / sizeof(T);  // k field, in elements after u
+    RingPos wpos, rpos;  // next plane to wait for / to release
+    bool failed = false;
+    auto wait_plane = [&]() -> bool {
+        if (!g.wait_full(wpos.slot, wpos.phase)) return false;
+        wpos.advance(g.ns);
+        return true;
+    };
+    auto release_plane = [&]() {
+        g.release(rpos.slot, lane);
+        rpos.advance(g.ns);
+    };
+
+    for (long long w = wk.w_first; w < wk.w_end && !failed;) {
+        const RingPiece q = wk.piece_at(w);
+        w += q.z_end - q.z_begin;
+        const int ox = q.x0 + tx * VX, oy = q.y0 + ty;
+        const bool vec = aligned && ox + VX <= nx;
+        const int nvalid = nx - ox;
+        // prologue: planes z_begin - RZ .. z_begin + RZ - 1
+        for (int k = 0; k < 2 * RZ && !failed; ++k) failed = !wait_plane();
+        for (int zo = q.z_begin; zo < q.z_end && !failed; ++zo) {
+            if (!wait_plane()) {  // plane zo + RZ
+                failed = true;
+                break;
+            }
+            // slots of planes zo - 1, zo, zo + 1 (wpos is one past zo + RZ)
+            int s0 = wpos.slot - 1 - RZ;
+            if (s0 < 0) s0 += g.ns;
+            const T *su = reinterpret_cast<const T *>(g.slot_ptr(s0));
+            const bool active = oy < ny && ox < nx;
             float acc[VX];
 #pragma unroll
             for (int i = 0; i < VX; ++i) acc[i] = 0.0f;
-            // Each face adds (k_c + k_n) (u_n - u_c); the sum is halved at the end (exact, so
-            // this equals the half-face form bit for bit).  A neighbour outside a Dirichlet
-            // grid has u = 0 and k = k_c.  ALLIN: no neighbour of this thread's cells is
-            // outside the grid, so no face needs a select.
-            auto compute = [&](auto allin_c) {
-                constexpr bool ALLIN = decltype(allin_c)::value;
-                auto face = [&](int i, float un, float kn, bool inside) {
-                    const float kc = k0[i + 1];
-                    const bool in = ALLIN || inside;
-                    const float ssum = kc + (in ? kn : kc);
-                    const float d = (in ? un : 0.0f) - u0[i + 1];
-                    acc[i] = fmaf(ssum, d, acc[i]);
+            if (active) {
+                const int i0 = off;
+                float u0[VX + 2], k0[VX + 2];  // centre row with one cell each side
+                load_span<T, -1, VX + 1, -1>(su + i0, u0);
+                load_span<T, -1, VX + 1, -1>(su + kofs + i0, k0);
+                // Each face adds (k_c + k_n) (u_n - u_c); the sum is halved at the end (exact,
+                // so this equals the half-face form bit for bit).  A neighbour outside a
+                // Dirichlet grid has u = 0 and k = k_c.  ALLIN: no neighbour of this thread's
+                // cells is outside the grid, so no face needs a select.
+                auto compute = [&](auto allin_c) {
+                    constexpr bool ALLIN = decltype(allin_c)::value;
+                    auto face = [&](int i, float un, float kn, bool inside) {
+                        const float kc = k0[i + 1];
+                        const bool in = ALLIN || inside;
+                        const float ssum = kc + (in ? kn : kc);
+                        const float d = (in ? un : 0.0f) - u0[i + 1];
+                        acc[i] = fmaf(ssum, d, acc[i]);
+                    };
+                    // axes in the oracle's order: z, y, x; within an axis the + face, then -
+                    if constexpr (NDIM == 3) {
+                        const int sp = s0 + 1 == g.ns ? 0 : s0 + 1;
+                        const int sm = s0 == 0 ? g.ns - 1 : s0 - 1;
+                        const T *up_ = reinterpret_cast<const T *>(g.slot_ptr(sp)) + i0;
+                        const T *um_ = reinterpret_cast<const T *>(g.slot_ptr(sm)) + i0;
+                        float up[VX], kp[VX], um[VX], km[VX];
+                        load_span<T, 0, VX, 0>(up_, up);
+                        load_span<T, 0, VX, 0>(up_ + kofs, kp);
+                        load_span<T, 0, VX, 0>(um_, um);
+                        load_span<T, 0, VX, 0>(um_ + kofs, km);
+                        const bool inp = periodic || zo + 1 < nz, inm = periodic || zo - 1 >= 0;
+#pragma unroll
+                        for (int i = 0; i < VX; ++i) {
+                            face(i, up[i], kp[i], inp);
+                            face(i, um[i], km[i], inm);
+                        }
+                    }
+                    {
+                        float up[VX], kp[VX], um[VX], km[VX];
+                        load_span<T, 0, VX, 0>(su + i0 + PITCH, up);
+                        load_span<T, 0, VX, 0>(su + kofs + i0 + PITCH, kp);
+                        load_span<T, 0, VX, 0>(su + i0 - PITCH, um);
+                        load_span<T, 0, VX, 0>(su + kofs + i0 - PITCH, km);
+                        const bool inp = periodic || oy + 1 < ny, inm = periodic || oy - 1 >= 0;
+#pragma unroll
+                        for (int i = 0; i < VX; ++i) {
+                            face(i, up[i], kp[i], inp);
+                            face(i, um[i], km[i], inm);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < VX; ++i) {
+                        const bool inp = periodic || ox + i + 1 < nx;
+                        const bool inm = periodic || ox + i - 1 >= 0;
+                        face(i, u0[i + 2], k0[i + 2], inp);
+                        face(i, u0[i], k0[i], inm);
+                    }
                 };
-                // axes in the oracle's order: z, y, x; within an axis the + face then the - face
-                if constexpr (NDIM == 3) {
-                    const int sp = slot_of(zo + 1) * plane_elems + off;
-                    const int sm = slot_of(zo - 1) * plane_elems + off;
-                    float up[VX], kp[VX], um[VX], km[VX];
-                    load_span<T, 0, VX, 0>(su + sp, up);
-                    load_span<T, 0, VX, 0>(sk + sp, kp);
-                    load_span<T, 0, VX, 0>(su + sm, um);
-                    load_span<T, 0, VX, 0>(sk + sm, km);
-                    const bool inp = periodic || zo + 1 < nz, inm = periodic || zo - 1 >= 0;
+                const bool all_in = periodic || (ox > 0 && ox + VX < nx && oy > 0 && oy + 1 < ny &&
+                                                 (NDIM == 2 || (zo > 0 && zo + 1 < nz)));
+                if (all_in)
+                    compute(std::true_type{});
+                else
+                    compute(std::false_type{});
+            }
+            release_plane();  // plane zo - RZ has been read for the last time (whole warp)
+            if (active) {
 #pragma unroll
-                    for (int i = 0; i < VX; ++i) {
-                        face(i, up[i], kp[i], inp);
-                        face(i, um[i], km[i], inm);
-                    }
-                }
-                {
-                    float up[VX], kp[VX], um[VX], km[VX];
-                    load_span<T, 0, VX, 0>(su + s0 + PITCH, up);
-                    load_span<T, 0, VX, 0>(sk + s0 + PITCH, kp);
-                    load_span<T, 0, VX, 0>(su + s0 - PITCH, um);
-                    load_span<T, 0, VX, 0>(sk + s0 - PITCH, km);
-                    const bool inp = periodic || oy + 1 < ny, inm = periodic || oy - 1 >= 0;
-#pragma unroll
-                    for (int i = 0; i < VX; ++i) {
-                        face(i, up[i], kp[i], inp);
-                        face(i, um[i], km[i], inm);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < VX; ++i) {
-                    const bool inp = periodic || ox + i + 1 < nx, inm = periodic || ox + i - 1 >= 0;
-                    face(i, u0[i + 2], k0[i + 2], inp);
-                    face(i, u0[i], k0[i], inm);
-                }
-            };
-            const bool all_in = periodic || (ox > 0 && ox + VX < nx && oy > 0 && oy + 1 < ny &&
-                                             (NDIM == 2 || (zo > 0 && zo + 1 < nz)));
-            if (all_in)
-                compute(std::true_type{});
-            else
-                compute(std::false_type{});
-#pragma unroll
-            for (int i = 0; i < VX; ++i) acc[i] *= 0.5f;
-            store_cells<T, VX>(p.out + (size_t)zo * pstride + (size_t)oy * nx + ox, vec, nvalid,
-                               acc);
+                for (int i = 0; i < VX; ++i) acc[i] *= 0.5f;
+                store_cells<T, VX>(p.out + (size_t)zo * pstride + (size_t)oy * nx + ox, vec,
+                                   nvalid, acc);
+            }
         }
-        __syncthreads();
+        // the last 2RZ planes of the piece were only read as neighbours
+        for (int k = 0; k < 2 * RZ && !failed; ++k) release_plane();
     }
-    cp_async_wait<0>();
+    if (failed) g.fail(p.err, lane);
 }
 
 }  // namespace gst

@@ -1,7 +1,10 @@
 // Host-side launchers of the variable-coefficient and div(k grad u) kernels.
 #pragma once
 
+#include <algorithm>
+
 #include "internal.h"
+#include "ring_launch.cuh"
 #include "var.cuh"
 
 namespace gst {
@@ -80,40 +83,61 @@ template <typename T, bool ADJ> int launch_var_dt(const VarLaunch &L) {
     return -1;
 }
 
-template <typename T> int launch_divkgrad_t(const VarLaunch &L) {
-    constexpr int VX = 16 / (int)sizeof(T), BX = 128 / VX, PITCH = 128 + 2 * VX;
-    const int by = L.block_y > 0 ? L.block_y : 8;
-    if (BX * by > 256 || (BX * by) % 32) return -1;
-    VarParams<T> p;
-    fill_var_params<T>(L, p, by);
-    const int nslot = L.ndim == 3 ? 4 : 2;
-    const int64_t zchunks = L.ndim == 3 ? (p.nz + p.zchunk - 1) / p.zchunk : 1;
-    const int64_t nblocks = (int64_t)p.tiles_x * p.tiles_y * zchunks;
-    if (nblocks > INT32_MAX) return -2;
-    const size_t smem = 2 * (size_t)nslot * PITCH * (by + 2) * sizeof(T);
-    if (L.ndim == 3) {
-        auto kern = divkgrad_kernel<T, 3>;
-        static size_t set3 = 0;
-        if (smem > 48 * 1024 && smem > set3) {
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return -4;
-            set3 = smem;
-        }
-        kern<<<(unsigned)nblocks, dim3(BX, by), smem, L.stream>>>(p);
-    } else {
-        auto kern = divkgrad_kernel<T, 2>;
-        static size_t set2 = 0;
-        if (smem > 48 * 1024 && smem > set2) {
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return -4;
-            set2 = smem;
-        }
-        kern<<<(unsigned)nblocks, dim3(BX, by), smem, L.stream>>>(p);
+template <typename T, int NDIM> int launch_divkgrad_nd(const VarLaunch &L) {
+    using K = DivkKernel<T, NDIM>;
+    auto kern = divkgrad_kernel<T, NDIM>;
+    int by = L.block_y > 0 ? L.block_y : 128 / K::BX;
+    by = std::min(by, K::MAX_THREADS / K::BX);
+    if ((K::BX * by) % 32) return -1;
+    const int64_t nx = L.nx, ny = L.ny, nz = NDIM == 3 ? L.nz : 1;
+    if (nx * ny > (int64_t)INT32_MAX - 4 * K::TX) return -2;
+    DivkParams<T> p;
+    p.field[0] = static_cast<const T *>(L.in);
+    p.field[1] = static_cast<const T *>(L.arrays[0]);
+    p.out = static_cast<T *>(L.out);
+    p.nx = (int)nx;
+    p.ny = (int)ny;
+    p.nz = (int)nz;
+    p.periodic = L.periodic;
+    const bool ptr_ok = (uintptr_t)L.in % 16 == 0 && (uintptr_t)L.arrays[0] % 16 == 0 &&
+                        (uintptr_t)L.out % 16 == 0;
+    p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
+    p.tiles_x = (int)((nx + K::TX - 1) / K::TX);
+    p.tiles_y = (int)((ny + by - 1) / by);
+    p.err = nullptr;
+    const int rows = by + 2;
+    p.use_tma = (p.aligned &&
+                 encode_plane_map<T>(&p.tmap[0], L.in, nx, ny, nz, K::PITCH, rows) &&
+                 encode_plane_map<T>(&p.tmap[1], L.arrays[0], nx, ny, nz, K::PITCH, rows))
+                    ? 1
+                    : 0;
+    const int threads = K::BX * by + 32;
+    // consumers hold the 2RZ+1 planes of their window: the ring needs at least one more
+    p.nstage = std::max(2 * K::RZ + 2, ring_stages(0, NDIM, reinterpret_cast<const void *>(kern),
+                                                   threads, 2 * K::field_bytes(by)));
+    const size_t smem = K::smem_bytes(by, p.nstage);
+    static size_t smem_set = 0;
+    if (smem > 48 * 1024 && smem > smem_set) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+            return -4;
+        smem_set = smem;
     }
+    // z chunks of z_chunk planes per CTA (whole columns when 0)
+    const int64_t total = (int64_t)p.tiles_x * p.tiles_y * nz;
+    const int64_t work = (NDIM == 3 && L.z_chunk > 0) ? L.z_chunk : nz;
+    p.work = (int)std::min<int64_t>(work, INT32_MAX);
+    const int64_t nblocks = (total + p.work - 1) / p.work;
+    if (nblocks > INT32_MAX) return -2;
+    kern<<<(unsigned)nblocks, dim3(K::BX, by + 32 / K::BX), smem, L.stream>>>(p);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+template <typename T> int launch_divkgrad_t(const VarLaunch &L) {
+    return L.ndim == 3 ? launch_divkgrad_nd<T, 3>(L) : launch_divkgrad_nd<T, 2>(L);
 }
 
 }  // namespace gst

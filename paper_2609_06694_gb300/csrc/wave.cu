@@ -1,9 +1,9 @@
 // Acoustic wave equation: leapfrog forward step, adjoint step, FP64 misfit and gradient, and
 // the checkpointed driver behind include/wave.h.
 //
-// Both step kernels evaluate the radius-R star Laplacian L of a field held in a ring of
-// 2R+2 shared-memory planes (cp.async, zero-filled ghosts), one output plane at a time, and
-// fuse the rest of the update into the same pass:
+// Both steps run the streaming star kernel (the radius-R Laplacian L of a field with zero
+// Dirichlet ghosts, tensor-copied plane by plane by a producer warp) with a fused epilogue
+// that applies the rest of the update to each finished output:
 //   forward:  u^{n+1} = 2u^n - u^{n-1} + a (.) L u^n (+ dt^2 s_n at the source cell),
 //             optionally storing L u^n (segment recompute) and the receiver plane;
 //   adjoint:  mu^m = 2mu^{m+1} - mu^{m+2} + a (.) L mu^{m+1} + a (.) r^m (receiver plane),
@@ -21,138 +21,93 @@
 #include "../../include/stencil.h"
 #include "../../include/wave.h"
 #include "internal.h"
+#include "stream_launch.cuh"
 #include "var.cuh"
 
 namespace gst {
 
-struct WaveParams {
-    const float *u;       // field under the stencil (u^n, or mu^{m+1})
-    const float *uprev;   // u^{n-1}, or mu^{m+2}
-    const float *a;       // (v dt / h)^2
-    float *unext;         // u^{n+1}, or mu^m
-    float *lu_store;      // forward: L u^n (optional)
-    float *trace_row;     // forward: receiver plane of u^{n+1} (optional)
-    const float *res_t;   // adjoint: trace row of step m
-    const float *res_o;   // adjoint: observed row of step m
-    const float *lu_prev; // adjoint: L u^{m-1}
-    double *G;            // adjoint: sum of mu^m L u^{m-1}
-    int nx, ny, nz;
-    int tiles_x, tiles_y, zchunk;
-    int aligned;
-    long long src;        // linear index of the source cell, -1 for none
-    float src_val;        // dt^2 s_n
-    int rz;
-    float c[25];          // star weights, canonical order
-};
-
-template <int R, bool ADJ>
-__global__ void __launch_bounds__(256) wave_step_kernel(const __grid_constant__ WaveParams p) {
-    constexpr int VX = 4, A = 4, TX = 128, BX = 32, PITCH = TX + 2 * A;
-    constexpr int NSLOT = 2 * R + 2;
-    using OT = OffsetTable<3, kStar, R>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *smem = reinterpret_cast<float *>(smem_raw);
-    const int by = blockDim.y, tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * BX + tx, nthr = BX * by;
-    const int rows = by + 2 * R;
-    const int plane_elems = PITCH * rows;
-    int b = blockIdx.x;
-    const int tix = b % p.tiles_x;
-    b /= p.tiles_x;
-    const int tiy = b % p.tiles_y, tiz = b / p.tiles_y;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int x0 = tix * TX, y0 = tiy * by;
-    const int z_begin = tiz * p.zchunk, z_end = min(nz, z_begin + p.zchunk);
-    const bool aligned = p.aligned != 0;
-    const size_t pstride = (size_t)nx * ny;
-    const int ox = x0 + tx * VX, oy = y0 + ty;
-    const bool vec = aligned && ox + VX <= nx;
-    const int nvalid = nx - ox;
-    float creg[OT::count];
+// The fused update applied to each finished Laplacian row segment L (VY rows of 4 cells at
+// (zo, oy, ox)) by the streaming star kernel, whose input `in` is the field under the stencil.
+//   forward:  u^{n+1} = 2u^n - u^{n-1} + a (.) L u^n (+ dt^2 s_n at the source cell),
+//             optionally storing L u^n and the receiver plane of u^{n+1};
+//   adjoint:  mu^m = 2mu^{m+1} - mu^{m+2} + a (.) L mu^{m+1} (+ a (.) r^m on the receiver
+//             plane), then G += mu^m (.) L u^{m-1} in FP64.
+template <bool ADJ> struct WaveEpi {
+    struct Params {
+        const float *uprev;    // u^{n-1}, or mu^{m+2}
+        const float *a;        // (v dt / h)^2
+        float *unext;          // u^{n+1}, or mu^m
+        float *lu_store;       // forward: L u^n (optional)
+        float *trace_row;      // forward: receiver plane of u^{n+1} (optional)
+        const float *res_t;    // adjoint: trace row of step m
+        const float *res_o;    // adjoint: observed row of step m
+        const float *lu_prev;  // adjoint: L u^{m-1}
+        double *G;             // adjoint: sum of mu^m L u^{m-1}
+        long long src;         // linear index of the source cell, -1 for none
+        float src_val;         // dt^2 s_n
+        int rz;                // receiver plane
+    };
+    // u^n (or mu^{m+1}) at the output, u^{n-1} (or mu^{m+2}), a, and for the adjoint L u^{m-1}
+    template <int VY, int VX> struct Regs {
+        float uc[VY][VX], up[VY][VX], av[VY][VX], lu[ADJ ? VY : 1][VX];
+    };
+    template <typename T, int VY, int VX>
+    __device__ __forceinline__ static void prefetch(const StreamParams<T> &p, const Params &e,
+                                                    int zo, int oy, int ox, bool vec,
+                                                    int vy_valid, Regs<VY, VX> &r) {
+        static_assert(sizeof(T) == 4, "the wave fields are f32");
+        const int nx = p.nx, nvalid = nx - ox;
 #pragma unroll
-    for (int i = 0; i < OT::count; ++i) creg[i] = p.c[i];
-
-    auto slot_of = [&](int zi) { return ((zi - z_begin + R) % NSLOT + NSLOT) % NSLOT; };
-    TileLoader<float, R, A, PITCH> loader;
-    loader.init(x0, y0, rows, nx, ny, nz, false, aligned, true, tid, nthr);
-    auto load = [&](int zi) { loader.load(p.u, smem + slot_of(zi) * plane_elems, zi); };
-    for (int zi = z_begin - R; zi <= z_begin + R; ++zi) {
-        load(zi);
-        cp_async_commit();
+        for (int vy = 0; vy < VY; ++vy) {
+            if (vy >= vy_valid) break;
+            const size_t base = ((size_t)zo * p.ny + oy + vy) * nx + ox;
+            load_cells<float, VX>(p.in + base, vec, nvalid, r.uc[vy]);
+            load_cells<float, VX>(e.uprev + base, vec, nvalid, r.up[vy]);
+            load_cells<float, VX>(e.a + base, vec, nvalid, r.av[vy]);
+            if constexpr (ADJ) load_cells<float, VX>(e.lu_prev + base, vec, nvalid, r.lu[vy]);
+        }
     }
-    const int off = (ty + R) * PITCH + A + tx * VX;
-    for (int zo = z_begin; zo < z_end; ++zo) {
-        if (zo + 1 < z_end) load(zo + R + 1);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
-        if (oy < ny && ox < nx) {
-            // pointwise operands first: their global-load latency overlaps the stencil below
-            const size_t base = (size_t)zo * pstride + (size_t)oy * nx + ox;
-            float up[VX], av[VX], lu[VX];
-            load_cells<float, VX>(p.uprev + base, vec, nvalid, up);
-            load_cells<float, VX>(p.a + base, vec, nvalid, av);
-            if constexpr (ADJ) load_cells<float, VX>(p.lu_prev + base, vec, nvalid, lu);
-            float L[VX], uc[VX];
+    template <typename T, int VY, int VX>
+    __device__ __forceinline__ static void apply(const StreamParams<T> &p, const Params &e,
+                                                 int zo, int oy, int ox, bool vec, int vy_valid,
+                                                 const Regs<VY, VX> &r,
+                                                 const float (&L)[VY][VX]) {
+        const int nx = p.nx, nvalid = nx - ox;
 #pragma unroll
-            for (int i = 0; i < VX; ++i) L[i] = 0.0f;
-            // canonical order: (dz, dy, dx) lexicographic
-            static_for<2 * R + 1>([&](auto dzi) {
-                constexpr int dz = decltype(dzi)::value - R;
-                const float *sp = smem + slot_of(zo + dz) * plane_elems + off;
-                static_for<2 * R + 1>([&](auto dyi) {
-                    constexpr int dy = decltype(dyi)::value - R;
-                    constexpr int m = OT::tab.mdx[dz + R][dy + R];
-                    if constexpr (m >= 0) {
-                        float win[VX + 2 * R];
-                        load_span<float, -m, VX + m, -R>(sp + dy * PITCH, win);
-                        if constexpr (dz == 0 && dy == 0) {
-#pragma unroll
-                            for (int i = 0; i < VX; ++i) uc[i] = win[i + R];
-                        }
-                        static_for<2 * R + 1>([&](auto dxi) {
-                            constexpr int dx = decltype(dxi)::value - R;
-                            constexpr int idx = OT::index(dz, dy, dx);
-                            if constexpr (idx >= 0) {
-#pragma unroll
-                                for (int i = 0; i < VX; ++i)
-                                    L[i] = fmaf(creg[idx], win[i + dx + R], L[i]);
-                            }
-                        });
-                    }
-                });
-            });
+        for (int vy = 0; vy < VY; ++vy) {
+            if (vy >= vy_valid) break;
+            const size_t row = (size_t)(oy + vy) * nx + ox;
+            const size_t base = (size_t)zo * nx * p.ny + row;
             float un[VX];
 #pragma unroll
-            for (int i = 0; i < VX; ++i) un[i] = fmaf(av[i], L[i], 2.0f * uc[i] - up[i]);
+            for (int i = 0; i < VX; ++i)
+                un[i] = fmaf(r.av[vy][i], L[vy][i], 2.0f * r.uc[vy][i] - r.up[vy][i]);
             if constexpr (!ADJ) {
-                if (p.src >= 0 && (long long)base <= p.src && p.src < (long long)base + VX) {
+                if (e.src >= 0 && (long long)base <= e.src && e.src < (long long)base + VX) {
 #pragma unroll
                     for (int i = 0; i < VX; ++i)
-                        if ((long long)base + i == p.src) un[i] += p.src_val;
+                        if ((long long)base + i == e.src) un[i] += e.src_val;
                 }
-                store_cells<float, VX>(p.unext + base, vec, nvalid, un);
-                if (p.lu_store) store_cells<float, VX>(p.lu_store + base, vec, nvalid, L);
-                if (p.trace_row && zo == p.rz)
-                    store_cells<float, VX>(p.trace_row + (size_t)oy * nx + ox, vec, nvalid, un);
+                store_cells<float, VX>(e.unext + base, vec, nvalid, un);
+                if (e.lu_store) store_cells<float, VX>(e.lu_store + base, vec, nvalid, L[vy]);
+                if (e.trace_row && zo == e.rz)
+                    store_cells<float, VX>(e.trace_row + row, vec, nvalid, un);
             } else {
-                if (zo == p.rz) {
+                if (zo == e.rz) {
                     float rt[VX], ro[VX];
-                    load_cells<float, VX>(p.res_t + (size_t)oy * nx + ox, vec, nvalid, rt);
-                    load_cells<float, VX>(p.res_o + (size_t)oy * nx + ox, vec, nvalid, ro);
+                    load_cells<float, VX>(e.res_t + row, vec, nvalid, rt);
+                    load_cells<float, VX>(e.res_o + row, vec, nvalid, ro);
 #pragma unroll
-                    for (int i = 0; i < VX; ++i) un[i] = fmaf(av[i], rt[i] - ro[i], un[i]);
+                    for (int i = 0; i < VX; ++i) un[i] = fmaf(r.av[vy][i], rt[i] - ro[i], un[i]);
                 }
-                store_cells<float, VX>(p.unext + base, vec, nvalid, un);
+                store_cells<float, VX>(e.unext + base, vec, nvalid, un);
 #pragma unroll
                 for (int i = 0; i < VX; ++i)
-                    if (i < nvalid) p.G[base + i] += (double)un[i] * (double)lu[i];
+                    if (i < nvalid) e.G[base + i] += (double)un[i] * (double)r.lu[vy][i];
             }
         }
-        __syncthreads();
     }
-    cp_async_wait<0>();
-}
+};
 
 __global__ void wave_a_kernel(const float *__restrict__ v, float *__restrict__ a, size_t n,
                               float dt_over_h) {
@@ -239,51 +194,54 @@ static int wave_step(wave_plan_s *p, bool adj, const float *u, const float *upre
                      float *lu_store, float *trace_row, const float *res_t, const float *res_o,
                      const float *lu_prev, double *G, long long src, float src_val,
                      cudaStream_t s) {
-    WaveParams q;
-    std::memset(&q, 0, sizeof(q));
-    q.u = u;
-    q.uprev = uprev;
-    q.a = p->a;
-    q.unext = unext;
-    q.lu_store = lu_store;
-    q.trace_row = trace_row;
-    q.res_t = res_t;
-    q.res_o = res_o;
-    q.lu_prev = lu_prev;
-    q.G = G;
-    q.nx = (int)p->nx;
-    q.ny = (int)p->ny;
-    q.nz = (int)p->nz;
-    const int by = 8;
-    q.tiles_x = (int)((p->nx + 127) / 128);
-    q.tiles_y = (int)((p->ny + by - 1) / by);
-    q.zchunk = 32;
-    q.aligned = (p->nx % 4 == 0) ? 1 : 0;
-    q.src = src;
-    q.src_val = src_val;
-    q.rz = (int)p->rz;
-    for (size_t i = 0; i < p->lap.size(); ++i) q.c[i] = p->lap[i];
-    const int zchunks = (int)((p->nz + q.zchunk - 1) / q.zchunk);
-    const unsigned nblocks = (unsigned)(q.tiles_x * q.tiles_y * zchunks);
-    const int R = p->radius;
-    const size_t smem = (size_t)(2 * R + 2) * (128 + 8) * (by + 2 * R) * sizeof(float);
-    // shared-memory opt-in already granted, per (radius, direction) kernel
-    static size_t smem_set[5][2] = {};
-    size_t &set = smem_set[R][adj ? 1 : 0];
-    auto go = [&](auto kern) -> int {
-        if (smem > set) {
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return STENCIL_ERR_CUDA;
-            set = smem;
-        }
-        kern<<<nblocks, dim3(32, by), smem, s>>>(q);
-        count_launch();
-        return cudaGetLastError() == cudaSuccess ? STENCIL_OK : STENCIL_ERR_CUDA;
-    };
-    if (R == 1) return adj ? go(wave_step_kernel<1, true>) : go(wave_step_kernel<1, false>);
-    if (R == 2) return adj ? go(wave_step_kernel<2, true>) : go(wave_step_kernel<2, false>);
-    return adj ? go(wave_step_kernel<4, true>) : go(wave_step_kernel<4, false>);
+    typename WaveEpi<false>::Params e;  // same layout for both directions
+    std::memset(&e, 0, sizeof(e));
+    e.uprev = uprev;
+    e.a = p->a;
+    e.unext = unext;
+    e.lu_store = lu_store;
+    e.trace_row = trace_row;
+    e.res_t = res_t;
+    e.res_o = res_o;
+    e.lu_prev = lu_prev;
+    e.G = G;
+    e.src = src;
+    e.src_val = src_val;
+    e.rz = (int)p->rz;
+    StreamLaunch L;
+    L.ndim = 3;
+    L.nz = p->nz;
+    L.ny = p->ny;
+    L.nx = p->nx;
+    L.shape = kStar;
+    L.radius = p->radius;
+    L.dtype = kF32;
+    L.periodic = 0;
+    L.coeffs = p->lap.data();
+    L.in = u;
+    L.out = unext;
+    L.block_x = 32;
+    L.block_y = 4;
+    L.vec_y = 1;
+    L.z_chunk = 32;
+    L.stages = 0;
+    L.err = nullptr;
+    L.stream = s;
+    int rc;
+    if (!adj) {
+        const typename WaveEpi<false>::Params &ef = e;
+        rc = p->radius == 1   ? launch_stream_t<float, 3, kStar, 1, 1, WaveEpi<false>>(L, ef)
+             : p->radius == 2 ? launch_stream_t<float, 3, kStar, 2, 1, WaveEpi<false>>(L, ef)
+                              : launch_stream_t<float, 3, kStar, 4, 1, WaveEpi<false>>(L, ef);
+    } else {
+        typename WaveEpi<true>::Params ea;
+        static_assert(sizeof(ea) == sizeof(e), "one parameter layout");
+        std::memcpy(&ea, &e, sizeof(e));
+        rc = p->radius == 1   ? launch_stream_t<float, 3, kStar, 1, 1, WaveEpi<true>>(L, ea)
+             : p->radius == 2 ? launch_stream_t<float, 3, kStar, 2, 1, WaveEpi<true>>(L, ea)
+                              : launch_stream_t<float, 3, kStar, 4, 1, WaveEpi<true>>(L, ea);
+    }
+    return rc == 0 ? STENCIL_OK : (rc == -2 ? STENCIL_ERR_UNSUPPORTED : STENCIL_ERR_CUDA);
 }
 
 static int wave_compute_a(wave_plan_s *p, const float *v, cudaStream_t s) {

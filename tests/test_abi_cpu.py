@@ -140,6 +140,15 @@ def test_variant_get_set_and_validation():
         gs.stencil_plan_set_variant(p, family=gs.FAMILY_FUSED2D, fuse=2, tile_x=32, tile_y=32,
                                     block_x=128, block_y=1)     # fused 2D on a 3D plan
     assert gs.stencil_plan_get_variant(p)["z_chunk"] == 16      # unchanged on failure
+    gs.stencil_plan_set_variant(p, stages=16)
+    assert gs.stencil_plan_get_variant(p)["stages"] == 16
+    for bad in (1, 17, -1):
+        with pytest.raises(gs.StencilError):
+            gs.stencil_plan_set_variant(p, stages=bad)          # ring depth 0 or 2..16
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(q := gs.stencil_plan(3, (64, 64, 64), "star", 1, "const",
+                                                         np.ones(7), "f32", "periodic"),
+                                    block_x=32, block_y=8)       # 256 consumer threads
     q = gs.stencil_plan(3, (64, 64, 64), "box", 4, "const", np.ones(729), "f32", "periodic")
     with pytest.raises(gs.StencilError):
         gs.stencil_plan_set_variant(q, vec_y=2)                  # not compiled for box r4
@@ -153,12 +162,16 @@ def test_variant_get_set_and_validation():
 def test_dispatch_map_file(tmp_path):
     m = tmp_path / "map.txt"
     m.write_text("# ndim shape r dtype bc kind class : family bx by vy zc fuse tx ty\n"
-                 "3 0 4 0 1 0 -1 : 1 32 8 1 48 1 0 0\n\n")
+                 "3 0 4 0 1 0 -1 : 1 32 8 1 48 1 0 0\n"
+                 "3 1 1 0 1 0 -1 : 1 32 4 2 32 1 0 0 6\n\n")
     gs.stencil_load_dispatch_map(str(m))
     try:
         p = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "periodic")
         v = gs.stencil_plan_get_variant(p)
         assert (v["block_x"], v["block_y"], v["vec_y"], v["z_chunk"]) == (32, 8, 1, 48)
+        assert v["stages"] == 0                                  # optional field absent
+        b = gs.stencil_plan(3, (64, 64, 64), "box", 1, "const", np.ones(27), "f32", "periodic")
+        assert gs.stencil_plan_get_variant(b)["stages"] == 6
         q = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "dirichlet")
         assert gs.stencil_plan_get_variant(q)["z_chunk"] != 48   # key differs (boundary)
         bad = tmp_path / "bad.txt"

@@ -84,17 +84,37 @@ def test_scalar_loader_odd_row_length(ndim, shape, bc):
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("vec_y", [1, 2])
-@pytest.mark.parametrize("blocks", [(32, 8), (32, 4), (32, 2), (32, 1)])
-def test_stream_variants_agree(shape, vec_y, blocks):
+@pytest.mark.parametrize("blocks", [(32, 7), (32, 4), (32, 3), (32, 1)])
+@pytest.mark.parametrize("stages", [0, 2, 5])
+def test_stream_variants_agree(shape, vec_y, blocks, stages):
+    # odd tile heights, the shallowest ring (the producer waits on every slot) and a ring
+    # deeper than some pieces are long
     r = 1
     dims = (19, 45, 200)
     offs = oracle.offsets(3, shape, r)
     c = seeded_weights(41, len(offs))
     plan = gs.stencil_plan(3, dims, shape, r, "const", c, "f32", "periodic")
     gs.stencil_plan_set_variant(plan, block_x=blocks[0], block_y=blocks[1], vec_y=vec_y,
-                                z_chunk=7)
+                                z_chunk=7, stages=stages)
     x, x64 = make_input(42, dims, "f32")
     assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, "periodic")) < 1e-5
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("stages", [2, 16])
+def test_stream_ring_depth_radius4(bc, stages):
+    # the 25-point star on a grid that is several tiles wide and tall with ragged edges, with
+    # the shallowest and the deepest ring and the 480-thread consumer tile
+    r = 4
+    dims = (40, 70, 300)
+    offs = oracle.offsets(3, "star", r)
+    c = seeded_weights(43, len(offs))
+    for by in (4, 15):
+        plan = gs.stencil_plan(3, dims, "star", r, "const", c, "f32", bc)
+        gs.stencil_plan_set_variant(plan, block_x=32, block_y=by, vec_y=1, z_chunk=9,
+                                    stages=stages)
+        x, x64 = make_input(44, dims, "f32")
+        assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, bc)) < 1e-5
 
 
 def test_tiny_grids_wrap_many_times():
