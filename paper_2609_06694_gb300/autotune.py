@@ -180,7 +180,8 @@ def main():
         lines.append(" ".join(map(str, key)) + " : " + " ".join(map(str, val)))
         evidence.append({"key": {"ndim": ndim, "dims": list(dims), "shape": shape, "radius": r,
                                  "dtype": dtype, "boundary": bc, "steps": steps,
-                                 "size_class": cls}, "candidates": ev})
+                                 "size_class": cls},
+                         "candidates_timed": len(ev), "fastest": ev[:10]})
     with open(args.out, "w") as f:
         f.write("\n".join(lines) + "\n")
     with open(args.evidence, "w") as f:
