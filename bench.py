@@ -147,20 +147,29 @@ def run_step(gs, W, stream, ev=None, only=None):
             ev.append((name, steps, s, e))
 
 
+def kernel_source_sha():
+    """sha256 prefix of the streaming kernel's sources (stream.cuh, then ring.cuh)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("stream.cuh", "ring.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_06694_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile(kernel_tag):
     """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
-    src = os.path.join(ROOT, "paper_2609_06694_gb300", "csrc", "stream.cuh")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha()
         vals = {}
         for ln in text.splitlines():
             if ln.startswith("- ") and ":" in ln:
                 k, v = ln[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-        if vals.get("stream.cuh sha256 prefix") != sha:
+        if vals.get("kernel source sha256 prefix") != sha:
             return None
         return float(vals["dram bytes per launch"])
     except Exception:

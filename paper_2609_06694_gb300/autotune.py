@@ -65,7 +65,8 @@ def fused2d_candidates(radius, steps):
     return out
 
 
-def time_variant(plan, xin, y, steps, variant, reps=5, warmup=2):
+def time_variant(plan, run, steps, variant, reps=5, warmup=2):
+    """Median time of run(plan, steps) with `variant` set; None if it cannot run."""
     import torch
     try:
         gs.stencil_plan_set_variant(plan, **variant)
@@ -73,13 +74,13 @@ def time_variant(plan, xin, y, steps, variant, reps=5, warmup=2):
         return None
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
-        gs.stencil_apply(plan, xin, y, steps)
+        run(plan, steps)
     ts = []
     for _ in range(reps):
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        gs.stencil_apply(plan, xin, y, steps)
+        run(plan, steps)
         e.record(stream)
         e.synchronize()
         ts.append(s.elapsed_time(e))
@@ -96,25 +97,46 @@ def hbm_peak():
         return 6800.0
 
 
-def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=print):
+def divkgrad_candidates(dtype, quick=False):
+    bx = 128 // (16 // (4 if dtype == "f32" else 2))
+    heights = (1, 2, 3, 4, 6, 7, 8, 12, 14) if not quick else (4, 7, 14)
+    out = []
+    for by, zc in itertools.product(heights, (0, 16, 32, 64, 128)):
+        if bx * by <= 224 and (bx * by) % 32 == 0:
+            out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=1,
+                            z_chunk=zc, fuse=1, tile_x=0, tile_y=0, stages=0))
+    return out
+
+
+def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=print,
+             kind="const"):
     """Time every candidate on `dims`; returns (best_variant, evidence list)."""
     import torch
-    c = inputs.normalised_abs_weights(7, _npts(ndim, shape, radius))
-    plan = gs.stencil_plan(ndim, dims, shape, radius, "const", c, dtype, bc)
     x = inputs.to_storage(inputs.uniform(8, dims), dtype).cuda()
     y = torch.empty_like(x)
-    cands = stream_candidates(ndim, shape, radius, dtype, quick)
-    if ndim == 2 and steps > 1:
-        cands += fused2d_candidates(radius, steps)
+    if kind == "divkgrad":
+        plan = gs.stencil_plan(ndim, dims, "star", 1, "divkgrad", None, dtype, bc)
+        k = inputs.to_storage(inputs.lognormal_k(4, dims), dtype).cuda()
+        cands = divkgrad_candidates(dtype, quick)
+        run = lambda p, n: gs.stencil_apply_var(p, x, [k], y, n)  # noqa: E731
+        bytes_per_cell = 3
+    else:
+        c = inputs.normalised_abs_weights(7, _npts(ndim, shape, radius))
+        plan = gs.stencil_plan(ndim, dims, shape, radius, "const", c, dtype, bc)
+        cands = stream_candidates(ndim, shape, radius, dtype, quick)
+        if ndim == 2 and steps > 1:
+            cands += fused2d_candidates(radius, steps)
+        run = lambda p, n: gs.stencil_apply(p, x, y, n)  # noqa: E731
+        bytes_per_cell = 2
     es = 4 if dtype == "f32" else 2
     cells = int(np.prod(dims))
     peak = hbm_peak()
     ev = []
     for v in cands:
-        ms = time_variant(plan, x, y, steps, v)
+        ms = time_variant(plan, run, steps, v)
         if ms is None:
             continue
-        gbs = 2 * es * cells * steps / (ms * 1e-3) / 1e9
+        gbs = bytes_per_cell * es * cells * steps / (ms * 1e-3) / 1e9
         ev.append({"variant": v, "ms": round(ms, 5), "alg_GBps": round(gbs, 1),
                    "frac_hbm": round(gbs / peak, 4)})
     ev.sort(key=lambda e: e["ms"])
@@ -135,12 +157,14 @@ def _npts(ndim, shape, r):
     return (2 * r + 1) * (2 * r * r + 2 * r + 3) // 3
 
 
-# Tuning set: (ndim, dims, shape, radius, dtype, boundary, steps)
+# Tuning set: (ndim, dims, shape, radius, dtype, boundary, steps, kind)
 def tuning_set(quick=False):
     s = []
     big = (512, 512, 512)
     for shape, r in (("star", 4), ("box", 1)):
         s.append((3, big, shape, r, "f32", "periodic", 1))
+    for dtype in ("f32",) if quick else ("f32", "f16", "bf16"):
+        s.append((3, (384, 384, 384), "star", 1, dtype, "dirichlet", 1, "divkgrad"))
     if not quick:
         mid = (384, 384, 384)
         for shape, r in (("star", 1), ("star", 2), ("box", 2), ("diamond", 2)):
@@ -169,17 +193,19 @@ def main():
              "# ndim shape radius dtype boundary kind size_class : "
              "family block_x block_y vec_y z_chunk fuse tile_x tile_y stages"]
     evidence = []
-    for ndim, dims, shape, r, dtype, bc, steps in tuning_set(args.quick):
-        best, ev = tune_key(ndim, dims, shape, r, dtype, bc, steps, args.quick)
+    for entry in tuning_set(args.quick):
+        ndim, dims, shape, r, dtype, bc, steps = entry[:7]
+        kind = entry[7] if len(entry) > 7 else "const"
+        best, ev = tune_key(ndim, dims, shape, r, dtype, bc, steps, args.quick, kind=kind)
         if best is None:
             continue
         cls = gs.stencil_size_class(int(np.prod(dims)))
-        key = [ndim, SHAPE_ID[shape], r, DTYPE_ID[dtype], BC_ID[bc], KIND_ID["const"], cls]
+        key = [ndim, SHAPE_ID[shape], r, DTYPE_ID[dtype], BC_ID[bc], KIND_ID[kind], cls]
         val = [best.get(k, 0) for k in ("family", "block_x", "block_y", "vec_y", "z_chunk",
                                         "fuse", "tile_x", "tile_y", "stages")]
         lines.append(" ".join(map(str, key)) + " : " + " ".join(map(str, val)))
         evidence.append({"key": {"ndim": ndim, "dims": list(dims), "shape": shape, "radius": r,
-                                 "dtype": dtype, "boundary": bc, "steps": steps,
+                                 "dtype": dtype, "boundary": bc, "steps": steps, "kind": kind,
                                  "size_class": cls},
                          "candidates_timed": len(ev), "fastest": ev[:10]})
     with open(args.out, "w") as f:

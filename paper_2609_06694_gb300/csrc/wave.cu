@@ -220,11 +220,13 @@ static int wave_step(wave_plan_s *p, bool adj, const float *u, const float *upre
     L.coeffs = p->lap.data();
     L.in = u;
     L.out = unext;
+    // measured on GB300 for the 256^3 radius-4 workload: 7 consumer rows per tile, 64-plane
+    // z chunks, a 4-deep ring
     L.block_x = 32;
-    L.block_y = 4;
+    L.block_y = 7;
     L.vec_y = 1;
-    L.z_chunk = 32;
-    L.stages = 0;
+    L.z_chunk = 64;
+    L.stages = 4;
     L.err = nullptr;
     L.stream = s;
     int rc;
