@@ -103,18 +103,31 @@ def test_stream_variants_agree(shape, vec_y, blocks, stages):
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
 @pytest.mark.parametrize("stages", [2, 16])
 def test_stream_ring_depth_radius4(bc, stages):
-    # the 25-point star on a grid that is several tiles wide and tall with ragged edges, with
-    # the shallowest and the deepest ring and the 480-thread consumer tile
-    r = 4
+    # wide stars on a grid that is several tiles wide and tall with ragged edges, with the
+    # shallowest and the deepest ring, up to the 480-thread consumer tile
     dims = (40, 70, 300)
-    offs = oracle.offsets(3, "star", r)
-    c = seeded_weights(43, len(offs))
-    for by in (4, 15):
+    for r, by in ((4, 4), (4, 8), (4, 15), (3, 15)):
+        offs = oracle.offsets(3, "star", r)
+        c = seeded_weights(43, len(offs))
         plan = gs.stencil_plan(3, dims, "star", r, "const", c, "f32", bc)
         gs.stencil_plan_set_variant(plan, block_x=32, block_y=by, vec_y=1, z_chunk=9,
                                     stages=stages)
         x, x64 = make_input(44, dims, "f32")
         assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, bc)) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape,r", [("star", 4), ("box", 1), ("star", 2)])
+def test_periodic_whole_tile_widths(dtype, shape, r):
+    # periodic grids whose width is a whole number of 128-cell tiles: the first and last tile
+    # columns wrap exactly one 16-byte chunk per row, patched over the tensor copy's zero
+    # fill; a single tile column is patched on both sides at once
+    for dims in ((20, 40, 256), (9, 33, 128)):
+        offs = oracle.offsets(3, shape, r)
+        c = seeded_weights(47, len(offs))
+        plan = gs.stencil_plan(3, dims, shape, r, "const", c, dtype, "periodic")
+        x, x64 = make_input(48, dims, dtype)
+        assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, "periodic")) < TOL[dtype]
 
 
 def test_tiny_grids_wrap_many_times():
