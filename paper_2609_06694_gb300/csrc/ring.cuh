@@ -144,10 +144,10 @@ template <typename T, int NF> struct RingSource {
 //  mode 2, TMA: lane 0 announces the bytes and issues one 3D tensor copy per field; the
 //    hardware zero-fills everything outside the grid (Dirichlet ghosts).
 //  mode 4, TMA + patches: a tile into which a periodic grid wraps takes the same tensor
-//    copies, on the slot's "tma" barrier; kLag planes later, once they have landed, the lanes
-//    copy the wrapped 16-byte chunks (whole rows above or below the grid, single chunks left
-//    or right of it) over the zero fill with cp.async and arrive on the full barrier when
-//    those have landed.
+//    copies, on the slot's "tma" barrier; once they have landed (the producer turns to it
+//    whenever no slot is free), the lanes copy the wrapped 16-byte chunks (whole rows above
+//    or below the grid, single chunks left or right of it) over the zero fill with cp.async
+//    and arrive on the full barrier when those have landed.
 //  mode 3, bulk rows: tiles with more wrapped chunks than the patch list holds (grids
 //    narrower than a tile): one bulk copy per contiguous segment of each row.
 //  mode 1, cp.async: no tensor map: 16-byte chunks of whole rows, wrapping or zero-filling.
@@ -163,7 +163,6 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
     const bool periodic = src.periodic;
     const size_t plane_stride = (size_t)nx * ny;
     const uint32_t plane_bytes = (uint32_t)(PITCH * rows * ES);
-    const int kLag = min(2, ns - 1);
     RingPos pos;
     bool ok = true;
     int issued = 0;      // planes issued so far (for the final drain)
@@ -332,28 +331,36 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
         };
 
         pslot = pos.slot;
-        int zp = q.zs;  // next plane of this piece to publish (mode 4)
-        for (int zi = q.zs; zi < q.zl; ++zi) {
-            if (!wait_all(g.empty_u32 + 8u * pos.slot, pos.phase ^ 1u)) {
-                ok = false;
-                break;
-            }
-            issue(zi);
-            // mode 4: publish the plane issued kLag planes ago (its copy has had time to land)
-            if (mode == 4 && zi + 1 - zp > kLag) {
-                if (!publish(zp)) {
+        if (mode != 4) {
+            for (int zi = q.zs; zi < q.zl; ++zi) {
+                if (!wait_all(g.empty_u32 + 8u * pos.slot, pos.phase ^ 1u)) {
                     ok = false;
                     break;
                 }
-                ++zp;
+                issue(zi);
             }
-        }
-        while (ok && mode == 4 && zp < q.zl) {
-            if (!publish(zp)) {
-                ok = false;
-                break;
+        } else {
+            // Patched planes: issue whenever a slot is free; otherwise publish the oldest
+            // issued plane (waiting for its tensor copy), otherwise wait for a slot.  So the
+            // publishing of a plane never waits for a slot (which would wait for consumers,
+            // which wait for published planes).
+            int zi = q.zs, zp = q.zs;  // next plane to issue / to publish
+            while (zp < q.zl) {
+                if (zi < q.zl &&
+                    __all_sync(0xffffffffu,
+                               mbar_test_wait(g.empty_u32 + 8u * pos.slot, pos.phase ^ 1u))) {
+                    issue(zi++);
+                } else if (zp < zi) {
+                    if (!publish(zp)) {
+                        ok = false;
+                        break;
+                    }
+                    ++zp;
+                } else if (!wait_all(g.empty_u32 + 8u * pos.slot, pos.phase ^ 1u)) {
+                    ok = false;
+                    break;
+                }
             }
-            ++zp;
         }
     }
     if (!ok) g.fail(err, lane);
