@@ -62,27 +62,35 @@ __device__ __forceinline__ void fused2d_tile(const T *__restrict__ in, T *__rest
     const bool x_in = gx0 >= 0 && gx0 + W <= t.nx;  // every column of the region is in the grid
     float *src = buf, *dst = buf + W * Hh;  // dst is used only when steps > 1
 
-    // load the tile with its halo, one warp per row (zero outside a Dirichlet grid)
+    // Load the tile with its halo (zero outside a Dirichlet grid), one warp per row: every lane
+    // issues its four loads of a 128-column block before it stores any of them.
     for (int r = warp; r < Hh; r += nwarps) {
         bool rok = true;
         const int gy = wrap_or_flag(gy0 + r, t.ny, periodic, rok);
         float *srow = src + r * W;
-        if (!rok) {
-            for (int c = lane; c < W; c += 32) srow[c] = 0.0f;
-            continue;
-        }
         const T *grow = in + (size_t)gy * t.nx;
-        if (x_in) {
-            for (int c = lane; c < W; c += 32) {
-                const T *a = grow + gx0 + c;
-                srow[c] = Storage<T>::to_float(COHERENT ? load_l2(a) : *a);
+        for (int cb = 0; cb < W; cb += 128) {
+            float v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = cb + lane + 32 * k;
+                v[k] = 0.0f;
+                if (rok && c < W) {
+                    if (x_in) {
+                        const T *a = grow + gx0 + c;
+                        v[k] = Storage<T>::to_float(COHERENT ? load_l2(a) : *a);
+                    } else {
+                        bool ok = true;
+                        const int gx = wrap_or_flag(gx0 + c, t.nx, periodic, ok);
+                        const T *a = grow + gx;
+                        if (ok) v[k] = Storage<T>::to_float(COHERENT ? load_l2(a) : *a);
+                    }
+                }
             }
-        } else {
-            for (int c = lane; c < W; c += 32) {
-                bool ok = true;
-                const int gx = wrap_or_flag(gx0 + c, t.nx, periodic, ok);
-                const T *a = grow + gx;
-                srow[c] = ok ? Storage<T>::to_float(COHERENT ? load_l2(a) : *a) : 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = cb + lane + 32 * k;
+                if (c < W) srow[c] = v[k];
             }
         }
     }
