@@ -17,7 +17,8 @@ struct StreamLaunch {
     const void *in;
     void *out;
     int block_x, block_y, vec_y, z_chunk;
-    int stages = 0;          // ring depth (0 = fill the shared memory, see stream_stages)
+    int stages = 0;          // ring depth (0 = fill the shared memory, see ring_stages)
+    int z_lo = 0, z_hi = -1; // 3D: output planes [z_lo, z_hi) only (z_hi < 0: to nz)
     int use_tma = 1;         // 0 forces the cp.async loader (tensor maps are used when legal)
     int *err;                // device error word or null
     cudaStream_t stream;

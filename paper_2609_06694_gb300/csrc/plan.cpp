@@ -180,9 +180,10 @@ int ensure_scratch(stencil_plan_s &p) {
     return STENCIL_OK;
 }
 
-// One launch of `k` steps from src to dst with the plan's variant and coefficients.
+// One launch of `k` steps from src to dst with the plan's variant and coefficients (3D
+// streaming plans: output planes [z_lo, z_hi) only, z_hi < 0 meaning all).
 static int launch_group(stencil_plan_s &p, const float *cf, const void *src, void *dst, int k,
-                        cudaStream_t s) {
+                        cudaStream_t s, int64_t z_lo = 0, int64_t z_hi = -1) {
     const stencil_variant &v = p.variant;
     if (v.family == STENCIL_FAMILY_FUSED2D) {
         Fused2DLaunch L;
@@ -219,6 +220,8 @@ static int launch_group(stencil_plan_s &p, const float *cf, const void *src, voi
     L.vec_y = v.vec_y;
     L.z_chunk = v.z_chunk;
     L.stages = v.stages;
+    L.z_lo = z_lo;
+    L.z_hi = z_hi;
     L.err = nullptr;
     L.stream = s;
     return map_launch_rc(launch_stream(L));
@@ -266,6 +269,89 @@ using namespace gst;
 // =========================================================================================
 // C ABI
 // =========================================================================================
+// stencil_apply_host for 3D streaming plans, pipelined over z slabs: the input slabs are
+// copied in on one stream; on the caller's stream a slab of output planes is swept as soon as
+// the input planes it reads have landed (the first sweep) or the previous sweep is done; the
+// finished output slabs of the last sweep are copied out on a third stream.  Both copy
+// directions overlap the sweeps and each other.  Slab k reads input planes up to R beyond
+// its end, so it waits for input slab k + 1; on a periodic grid slab 0 also reads the last
+// planes, so it is swept last.
+static int apply_host_pipelined(stencil_plan_s &h, const void *in_host, void *out_host,
+                                int steps, cudaStream_t s) {
+    constexpr int kMax = stencil_plan_s::kMaxSlabs;
+    const int64_t nz = h.dims[0];
+    const size_t plane = (size_t)h.dims[1] * h.dims[2] * dtype_size(h.dtype);
+    const int R = h.radius;
+    const bool periodic = h.boundary == STENCIL_PERIODIC;
+    const int nslab = (int)std::min<int64_t>(kMax, nz / std::max(16, 2 * R));
+    int64_t zb[kMax + 1];
+    for (int k = 0; k <= nslab; ++k) zb[k] = nz * k / nslab;
+    if (!h.s_in) {
+        bool ok = cudaStreamCreateWithFlags(&h.s_in, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h.s_out, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&h.ev_start, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&h.ev_done, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < kMax && ok; ++k)
+            ok = cudaEventCreateWithFlags(&h.ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h.ev_out[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return STENCIL_ERR_CUDA;
+        }
+    }
+    if (steps > 1) {
+        int rc = ensure_scratch(h);
+        if (rc) return rc;
+    }
+    auto check = [](cudaError_t e) { return e == cudaSuccess; };
+    // the copies start after whatever the caller queued before
+    if (!check(cudaEventRecord(h.ev_start, s)) || !check(cudaStreamWaitEvent(h.s_in, h.ev_start, 0)) ||
+        !check(cudaStreamWaitEvent(h.s_out, h.ev_start, 0)))
+        return STENCIL_ERR_CUDA;
+    const char *hin = static_cast<const char *>(in_host);
+    char *hout = static_cast<char *>(out_host);
+    char *din = static_cast<char *>(h.stage_in), *dout = static_cast<char *>(h.stage_out);
+    for (int k = 0; k < nslab; ++k) {
+        const size_t off = (size_t)zb[k] * plane, len = (size_t)(zb[k + 1] - zb[k]) * plane;
+        if (!check(cudaMemcpyAsync(din + off, hin + off, len, cudaMemcpyHostToDevice, h.s_in)) ||
+            !check(cudaEventRecord(h.ev_in[k], h.s_in)))
+            return STENCIL_ERR_CUDA;
+    }
+    const void *src = h.stage_in;
+    for (int g = 0; g < steps; ++g) {
+        void *dst = ((steps - 1 - g) % 2 == 0) ? h.stage_out : h.scratch;
+        const bool first = g == 0, last = g == steps - 1;
+        if (!first && !last) {
+            int rc = launch_group(h, h.cf.data(), src, dst, 1, s);
+            if (rc) return rc;
+        } else {
+            for (int j = 0; j < nslab; ++j) {
+                // periodic grids sweep slab 0 last (it reads the last input planes)
+                const int k = periodic ? (j + 1) % nslab : j;
+                if (first) {
+                    const int need = (periodic && k == 0) ? nslab - 1 : std::min(k + 1, nslab - 1);
+                    if (!check(cudaStreamWaitEvent(s, h.ev_in[need], 0))) return STENCIL_ERR_CUDA;
+                }
+                int rc = launch_group(h, h.cf.data(), src, dst, 1, s, zb[k], zb[k + 1]);
+                if (rc) return rc;
+                if (last) {
+                    const size_t off = (size_t)zb[k] * plane;
+                    const size_t len = (size_t)(zb[k + 1] - zb[k]) * plane;
+                    if (!check(cudaEventRecord(h.ev_out[k], s)) ||
+                        !check(cudaStreamWaitEvent(h.s_out, h.ev_out[k], 0)) ||
+                        !check(cudaMemcpyAsync(hout + off, dout + off, len,
+                                               cudaMemcpyDeviceToHost, h.s_out)))
+                        return STENCIL_ERR_CUDA;
+                }
+            }
+        }
+        src = dst;
+    }
+    if (!check(cudaEventRecord(h.ev_done, h.s_out)) || !check(cudaStreamWaitEvent(s, h.ev_done, 0)))
+        return STENCIL_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
 extern "C" {
 
 int stencil_abi_version(void) { return STENCIL_ABI_VERSION; }
@@ -366,11 +452,19 @@ int stencil_offsets(stencil_handle h, int32_t *offsets_out, int64_t capacity, in
 
 int stencil_destroy(stencil_handle h) {
     if (!h) return STENCIL_OK;
-    if (h->scratch || h->stage_in || h->stage_out || h->d_err) cudaDeviceSynchronize();
+    if (h->scratch || h->stage_in || h->stage_out || h->d_err || h->s_in) cudaDeviceSynchronize();
     if (h->scratch) cudaFree(h->scratch);
     if (h->stage_in) cudaFree(h->stage_in);
     if (h->stage_out) cudaFree(h->stage_out);
     if (h->d_err) cudaFree(h->d_err);
+    for (int i = 0; i < stencil_plan_s::kMaxSlabs; ++i) {
+        if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
+        if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_done) cudaEventDestroy(h->ev_done);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
     delete h;
     return STENCIL_OK;
 }
@@ -407,6 +501,9 @@ int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, in
         h->stage_bytes = bytes;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->ndim == 3 && h->variant.family == STENCIL_FAMILY_STREAM &&
+        h->dims[0] >= 2 * std::max(16, 2 * h->radius))
+        return apply_host_pipelined(*h, in_host, out_host, steps, s);
     if (cudaMemcpyAsync(h->stage_in, in_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return STENCIL_ERR_CUDA;
     int rc = run_steps(*h, h->cf.data(), h->stage_in, h->stage_out, steps, s);

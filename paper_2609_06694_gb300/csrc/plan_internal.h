@@ -5,6 +5,8 @@
 
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/stencil.h"
 
 struct stencil_plan_s {
@@ -23,6 +25,11 @@ struct stencil_plan_s {
     void *stage_out = nullptr;
     size_t stage_bytes = 0;
     int *d_err = nullptr;          // device error word (allocated by the kernels that need one)
+    // stencil_apply_host's z-slab pipeline: copy-in and copy-out streams and their events
+    static constexpr int kMaxSlabs = 8;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[kMaxSlabs] = {}, ev_out[kMaxSlabs] = {}, ev_start = nullptr,
+                ev_done = nullptr;
 };
 
 namespace gst {

@@ -94,19 +94,21 @@ struct RingPos {
     }
 };
 
-// A CTA's work: planes [w_first, w_end) of the flattened (tile, z) sequence (tiles in
-// row-major order, z fastest), possibly spanning several tiles; each piece is one z-stream
-// of a tile, read with RZ extra planes on each side.
+// A CTA's work: planes [w_first, w_end) of the flattened (tile, z) sequence over the z range
+// [zoff, zoff + nz) (tiles in row-major order, z fastest), possibly spanning several tiles;
+// each piece is one z-stream of a tile, read with RZ extra planes on each side.
 struct RingPiece {
     int x0, y0, z_begin, z_end, zs, zl;
 };
 struct RingWork {
     long long w_first, w_end;
     int nzp, tiles_x, TX, TY, RZ;
+    int zoff;  // first plane of the z range the sequence covers (nz planes from it)
     __device__ __forceinline__ void setup(int tiles_x_, int tiles_y, int nz, int work, int TX_,
-                                          int TY_, int RZ_) {
+                                          int TY_, int RZ_, int zoff_ = 0) {
         tiles_x = tiles_x_;
         nzp = nz;
+        zoff = zoff_;
         TX = TX_;
         TY = TY_;
         RZ = RZ_;
@@ -117,8 +119,9 @@ struct RingWork {
     __device__ __forceinline__ RingPiece piece_at(long long w) const {
         RingPiece q;
         const int tile = (int)(w / nzp);
-        q.z_begin = (int)(w % nzp);
-        q.z_end = (int)min((long long)nzp, (long long)q.z_begin + (w_end - w));
+        const int zr = (int)(w % nzp);
+        q.z_begin = zoff + zr;
+        q.z_end = zoff + (int)min((long long)nzp, (long long)zr + (w_end - w));
         const int tix = tile % tiles_x, tiy = tile / tiles_x;
         q.x0 = tix * TX;
         q.y0 = tiy * TY;

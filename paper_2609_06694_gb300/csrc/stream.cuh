@@ -147,6 +147,7 @@ template <typename T> struct StreamParams {
     int work;           // planes per CTA (flattened tile x z sequence)
     int use_tma;        // 1 = tensor-map loads (tmap describes `in`)
     int nstage;         // ring slots, 2 .. kMaxStages
+    int z_lo, z_cnt;    // output planes [z_lo, z_lo + z_cnt) (3D; 0, 1 for 2D)
     int *err;           // device error word (may be null)
 };
 
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(
     const int nx = p.nx, ny = p.ny;
     const bool aligned = p.aligned != 0;
     RingWork wk;
-    wk.setup(p.tiles_x, p.tiles_y, NDIM == 3 ? p.nz : 1, p.work, TX, TY, RZ);
+    wk.setup(p.tiles_x, p.tiles_y, p.z_cnt, p.work, TX, TY, RZ, p.z_lo);
 
     if (tid >= ncons) {
         // producer warp

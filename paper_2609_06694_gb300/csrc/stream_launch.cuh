@@ -45,6 +45,10 @@ int launch_stream_t(const StreamLaunch &L,
     p.periodic = L.periodic;
     p.tiles_x = (int)((nx + TX - 1) / TX);
     p.tiles_y = (int)((ny + TY - 1) / TY);
+    p.z_lo = NDIM == 3 ? (int)std::max<int64_t>(0, L.z_lo) : 0;
+    const int64_t z_hi = NDIM == 3 ? (L.z_hi < 0 ? nz : std::min<int64_t>(L.z_hi, nz)) : 1;
+    if (z_hi <= p.z_lo) return 0;  // nothing to sweep
+    p.z_cnt = (int)(z_hi - p.z_lo);
     const bool ptr_ok = ((uintptr_t)L.in % 16 == 0) && ((uintptr_t)L.out % 16 == 0);
     p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
     p.err = L.err;
@@ -76,7 +80,7 @@ int launch_stream_t(const StreamLaunch &L,
     // Work split: z_chunk > 0 gives every CTA z_chunk planes; z_chunk == 0 sizes the grid to
     // the CTAs that fit on the GPU at once (a multiple of the SM count) and gives each an equal
     // share of the (tile, z) planes.
-    const int64_t total = (int64_t)p.tiles_x * p.tiles_y * nz;
+    const int64_t total = (int64_t)p.tiles_x * p.tiles_y * p.z_cnt;
     int64_t work;
     if (L.z_chunk > 0) {
         work = L.z_chunk;

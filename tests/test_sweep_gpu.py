@@ -130,6 +130,35 @@ def test_periodic_whole_tile_widths(dtype, shape, r):
         assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, "periodic")) < TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("steps", [1, 2, 3])
+def test_apply_host_buffers(dtype, steps):
+    # stencil_apply_host: 3D grids deep enough for the z-slab pipeline (copies in and out
+    # overlapping the sweeps; a periodic grid sweeps its first slab last), a shallow one and a
+    # 2D one on the simple path; pinned and pageable host buffers.  Bit for bit equal to the
+    # device-buffer path, and within tolerance of the oracle.
+    cases = [(3, (70, 40, 256), "star", 4, "periodic"), (3, (130, 33, 128), "box", 1, "dirichlet"),
+             (3, (64, 20, 130), "diamond", 2, "periodic"), (3, (9, 20, 64), "star", 2, "periodic"),
+             (2, (90, 300), "box", 2, "periodic")]
+    for i, (ndim, dims, shape, r, bc) in enumerate(cases):
+        offs = oracle.offsets(ndim, shape, r)
+        c = seeded_weights(60 + i, len(offs))
+        plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, dtype, bc)
+        x, x64 = make_input(61 + i, dims, dtype)
+        for pinned in (True, False):
+            hin = x.pin_memory() if pinned else x.clone()
+            hout = torch.empty_like(hin)
+            if pinned:
+                hout = hout.pin_memory()
+            gs.stencil_apply_host(plan, hin, hout, steps)
+            dev = torch.empty_like(x.cuda())
+            gs.stencil_apply(plan, x.cuda(), dev, steps)
+            torch.cuda.synchronize()
+            assert torch.equal(hout, dev.cpu()), (dims, shape, bc, pinned)
+        pure, emu = oracle_run(x64, offs, c, bc, steps, dtype)
+        assert relerr(inputs.stored_values(hout), emu) < TOL[dtype]
+
+
 def test_tiny_grids_wrap_many_times():
     for ndim, dims in ((3, (3, 2, 4)), (3, (1, 1, 8)), (2, (1, 4)), (2, (3, 5)), (3, (2, 3, 5))):
         for shape in SHAPES:
