@@ -77,16 +77,21 @@ __device__ __forceinline__ void fma_n(float c, const float *w, float *a) {
 // Loads of a compile-time element range [LO, HI) from a 16-byte-aligned shared-memory base,
 // converted to float into dst[(e - LO0)] where LO0 is the window origin.
 // ---------------------------------------------------------------------------------------
+// The values of a 32-bit word of storage type T as floats (exact: every f16 and bf16 value
+// is a float).  A bfloat16 is the upper half of the float with the same value, so two integer
+// operations widen both halves; a pair of halves widens in one paired conversion.
 template <typename T> __device__ __forceinline__ void unpack(uint32_t bits, float *d, int n) {
     if constexpr (sizeof(T) == 4) {
         d[0] = __uint_as_float(bits);
+    } else if constexpr (Storage<T>::kDType == kBF16) {
+        d[0] = __uint_as_float(bits << 16);
+        if (n > 1) d[1] = __uint_as_float(bits & 0xFFFF0000u);
     } else {
-        T lo, hi;
-        uint16_t l = (uint16_t)(bits & 0xFFFFu), h = (uint16_t)(bits >> 16);
-        memcpy(&lo, &l, 2);
-        memcpy(&hi, &h, 2);
-        d[0] = Storage<T>::to_float(lo);
-        if (n > 1) d[1] = Storage<T>::to_float(hi);
+        __half2 h2;
+        memcpy(&h2, &bits, 4);
+        const float2 f = __half22float2(h2);
+        d[0] = f.x;
+        if (n > 1) d[1] = f.y;
     }
 }
 
