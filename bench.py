@@ -467,21 +467,48 @@ def suite():
                 "variant": gs.stencil_plan_get_variant(plan),
                 "note": "1 MiB grid stays in L2: latency-bound, not HBM-bound"})
 
-    # 3D 512^3 single and 8-step sweeps (the bench workload, per part)
+    # 3D 512^3 single and 8-step sweeps (the bench workload, per part), and the adjoint sweep
+    # (flipped coefficients through the same kernels) against the forward one
     W3 = build_workload(torch.device("cuda", 0))
     for name, xin in (("star", "x_star"), ("box", "x_box")):
+        label = '25-pt star r4' if name == 'star' else '27-pt box'
         for steps in (1, 8):
             ms = _time(lambda: gs.stencil_apply(W3[name], W3[xin], W3["y"], steps))
             gbs = 8 * CELLS * steps / (ms * 1e-3) / 1e9
-            out.append({"workload": f"3D 512^3 f32 periodic {'25-pt star r4' if name == 'star' else '27-pt box'}, {steps} step(s)",
+            out.append({"workload": f"3D 512^3 f32 periodic {label}, {steps} step(s)",
                         "ms": round(ms, 4), "Gcell_updates_per_s": round(CELLS * steps / ms / 1e6, 2),
                         "alg_GBps": round(gbs, 1), "frac_measured_hbm": round(gbs / peak, 4),
                         "frac_nominal_8TBps": round(gbs / 8000.0, 4)})
+        ms_f = _time(lambda: gs.stencil_apply(W3[name], W3[xin], W3["y"], 1))
+        ms_a = _time(lambda: gs.stencil_apply_adjoint(W3[name], W3[xin], W3["y"], 1))
+        out.append({"workload": f"3D 512^3 f32 periodic {label}, adjoint vs forward sweep",
+                    "ms_forward": round(ms_f, 4), "ms_adjoint": round(ms_a, 4),
+                    "adjoint_over_forward": round(ms_a / ms_f, 3)})
     del W3
     torch.cuda.empty_cache()
 
-    # div(k grad u) 384^3 in three storage types
+    # general variable coefficients (7 coefficient arrays, 3D star r1, 384^3): forward
+    # w_o[p] in[p+o] and adjoint w_o[q-o] in[q-o] (shifted gathers)
     n = 384
+    for dt in ("f32", "bf16"):
+        es = 4 if dt == "f32" else 2
+        plan = gs.stencil_plan(3, (n, n, n), "star", 1, "var", None, dt, "dirichlet")
+        u = inputs.to_storage(inputs.uniform(3101, (n, n, n)), dt).cuda()
+        w = [inputs.to_storage(inputs.uniform(3110 + i, (n, n, n)), dt).cuda() for i in range(7)]
+        y = torch.empty_like(u)
+        ms_f = _time(lambda: gs.stencil_apply_var(plan, u, w, y, 1))
+        ms_a = _time(lambda: gs.stencil_apply_adjoint_var(plan, u, w, y, 1))
+        gb = 9 * es * n ** 3 / 1e9
+        out.append({"workload": f"variable-coefficient star r1 384^3 {dt} Dirichlet, forward / adjoint",
+                    "ms_forward": round(ms_f, 4), "ms_adjoint": round(ms_a, 4),
+                    "adjoint_over_forward": round(ms_a / ms_f, 3),
+                    "alg_GBps_forward": round(gb / (ms_f * 1e-3), 1),
+                    "frac_measured_hbm_forward": round(gb / (ms_f * 1e-3) / peak, 4),
+                    "frac_measured_hbm_adjoint": round(gb / (ms_a * 1e-3) / peak, 4)})
+        del u, w, y
+    torch.cuda.empty_cache()
+
+    # div(k grad u) 384^3 in three storage types
     kk = inputs.lognormal_k(3002, (n, n, n))
     uu = inputs.uniform(3001, (n, n, n))
     for dt in ("f32", "f16", "bf16"):
