@@ -42,6 +42,25 @@ def rank_info():
     return r, w, lr
 
 
+def reduce_over_ranks(value, op="max"):
+    """MAX (or SUM) of a per-rank number over the ranks of the job (one process per GPU,
+    replicas only); the number itself when the job has a single rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(updates_per_rank, world, seconds):
+    """Whole-job Gcell-updates/s: every rank's updates over the slowest rank's time."""
+    return updates_per_rank * world / seconds / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -234,14 +253,9 @@ def bench_ours(args):
         dist.barrier()
     launches = gs.stencil_launch_count() - launches0
     clocks = sampler.stop()
-    ms_total = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_over_ranks(t0.elapsed_time(t1), "max")
     ms_per_step = ms_total / args.steps
-    updates = SWEEPS_PER_STEP * CELLS * args.steps * world
-    value = updates / (ms_total * 1e-3) / 1e9
+    value = job_throughput(SWEEPS_PER_STEP * CELLS * args.steps, world, ms_total * 1e-3)
 
     # per-kernel timing from the events: star r4 sweep kernel is the dominant kernel
     per = {"star": [0.0, 0], "box": [0.0, 0]}
@@ -282,12 +296,8 @@ def bench_ours(args):
         for _ in range(e2e_steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - h0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e_val = round(SWEEPS_PER_STEP * CELLS * e2e_steps * world / e2e_s / 1e9, 3)
+        e2e_s = reduce_over_ranks(time.perf_counter() - h0, "max")
+        e2e_val = round(job_throughput(SWEEPS_PER_STEP * CELLS * e2e_steps, world, e2e_s), 3)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
