@@ -28,7 +28,7 @@ struct StreamLaunch {
 // Most consumer threads of a streaming kernel's CTA (kept in step with
 // StreamKernel::MAX_THREADS); the CTA adds one producer warp.
 constexpr int stream_max_threads(int ndim, int shape, int radius, int vec_y) {
-    return (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 1) ? 480 : 224;
+    return (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 1) ? 256 : 224;
 }
 
 // Defined in stream_<dtype>_<ndim>d_<shape>.cu.

@@ -1,7 +1,8 @@
 // The plane ring shared by the streaming kernels: a CTA walks z-planes of a tile; one producer
 // warp keeps a ring of shared-memory slots filled with the input planes (NF fields per plane,
-// each a tile plus an R-row halo in y and one 16-byte chunk of halo in x) while the consumer
-// warps compute.  Each slot has three mbarriers:
+// each a tile plus an R-row halo in y and one 16-byte chunk of halo in x, then -- for kernels
+// that ask for them -- two side arrays holding the x halo chunks of a periodic edge tile)
+// while the consumer warps compute.  Each slot has three mbarriers:
 //   full  -- the plane is in the slot (32 arrivals of the producer warp, plus copied bytes),
 //   empty -- every consumer warp has finished reading it (one arrival per consumer warp),
 //   tma   -- its tensor copies have landed (periodic tiles that still need patches).
@@ -27,6 +28,14 @@ struct RingLayout {
     __host__ __device__ static constexpr uint32_t field_size(int pitch, int rows, int es) {
         return (uint32_t)(((size_t)pitch * rows * es + 127) / 128 * 128);
     }
+    // the side arrays of a slot: the left and then the right 16-byte halo chunk of every row,
+    // each array starting on a 128-byte boundary (tensor-copy destinations)
+    __host__ __device__ static constexpr uint32_t side_half(int rows) {
+        return (uint32_t)((16 * rows + 127) / 128 * 128);
+    }
+    __host__ __device__ static constexpr uint32_t side_size(int rows) {
+        return 2 * side_half(rows);
+    }
     __host__ __device__ static constexpr size_t bytes(uint32_t slot_bytes, int ns) {
         return (size_t)ns * (slot_bytes + 24) + 16 + 8 * kMaxPatches;
     }
@@ -35,16 +44,19 @@ struct RingLayout {
 struct Ring {
     unsigned char *base;
     uint32_t base_u32, field_bytes, slot_bytes;
+    uint32_t side_off;  // byte offset of the side arrays in a slot (after the NF fields)
     int ns;
     uint32_t full_u32, empty_u32, tma_u32;
     volatile int *abort_flag;
     uint2 *plist;
 
-    __device__ __forceinline__ void setup(unsigned char *smem, uint32_t fbytes, int nf, int nstage) {
+    __device__ __forceinline__ void setup(unsigned char *smem, uint32_t fbytes, int nf, int nstage,
+                                          uint32_t side_bytes = 0) {
         base = smem;
         base_u32 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
         field_bytes = fbytes;
-        slot_bytes = fbytes * nf;
+        side_off = fbytes * nf;
+        slot_bytes = fbytes * nf + side_bytes;
         ns = nstage;
         full_u32 = base_u32 + (uint32_t)ns * slot_bytes;
         empty_u32 = full_u32 + 8u * (uint32_t)ns;
@@ -96,23 +108,27 @@ struct RingPos {
 
 // A CTA's work: planes [w_first, w_end) of the flattened (tile, z) sequence over the z range
 // [zoff, zoff + nz) (tiles in row-major order, z fastest), possibly spanning several tiles;
-// each piece is one z-stream of a tile, read with RZ extra planes on each side.
+// each piece is one z-stream of a tile, read with RZ extra planes on each side.  The sequence
+// takes the two tile rows at the y ends of the grid first (tile row 0, then the last one, then
+// rows 1, 2, ...): on a periodic grid their rows wrap, their planes need patches and their
+// CTAs run longest, so they start in the first wave instead of trailing the launch.
 struct RingPiece {
     int x0, y0, z_begin, z_end, zs, zl;
 };
 struct RingWork {
     long long w_first, w_end;
-    int nzp, tiles_x, TX, TY, RZ;
+    int nzp, tiles_x, tiles_y, TX, TY, RZ;
     int zoff;  // first plane of the z range the sequence covers (nz planes from it)
-    __device__ __forceinline__ void setup(int tiles_x_, int tiles_y, int nz, int work, int TX_,
+    __device__ __forceinline__ void setup(int tiles_x_, int tiles_y_, int nz, int work, int TX_,
                                           int TY_, int RZ_, int zoff_ = 0) {
         tiles_x = tiles_x_;
+        tiles_y = tiles_y_;
         nzp = nz;
         zoff = zoff_;
         TX = TX_;
         TY = TY_;
         RZ = RZ_;
-        const long long total = (long long)tiles_x_ * tiles_y * nz;
+        const long long total = (long long)tiles_x_ * tiles_y_ * nz;
         w_first = (long long)blockIdx.x * work;
         w_end = min(total, w_first + (long long)work);
     }
@@ -122,7 +138,8 @@ struct RingWork {
         const int zr = (int)(w % nzp);
         q.z_begin = zoff + zr;
         q.z_end = zoff + (int)min((long long)nzp, (long long)zr + (w_end - w));
-        const int tix = tile % tiles_x, tiy = tile / tiles_x;
+        const int tix = tile % tiles_x, k = tile / tiles_x;
+        const int tiy = k == 0 ? 0 : (k == 1 ? tiles_y - 1 : k - 1);  // y ends first
         q.x0 = tix * TX;
         q.y0 = tiy * TY;
         q.zs = q.z_begin - RZ;
@@ -133,20 +150,40 @@ struct RingWork {
 
 // What the producer copies: NF fields of the grid (nz x ny x nx, x fastest) and, when rows
 // are 16-byte aligned and the driver could encode them, one 3D tensor map per field with the
-// box (PITCH, rows, 1).
+// box (PITCH, rows, 1).  With use_side (one field, periodic), side_tmap is a second map of the
+// same field with the box (A, rows, 1): one 16-byte column chunk of every row.
 template <typename T, int NF> struct RingSource {
-    const CUtensorMap *tmap;  // NF maps (kernel parameters)
-    const T *const *field;    // NF pointers
+    const CUtensorMap *tmap;       // NF maps (kernel parameters)
+    const CUtensorMap *side_tmap;  // the side map (use_side only)
+    const T *const *field;         // NF pointers
     int nx, ny, nz;
-    bool periodic, aligned, use_tma;
+    bool periodic, aligned, use_tma, use_side;
     int rows;
 };
+
+// Which x halo chunks of a piece come from the slot's side arrays: bit 0 the left chunk (the
+// tile starts at x = 0, so the chunk wraps to x = nx - A), bit 1 the right one (the tile ends
+// at x = nx, so it wraps to x = 0).  Only periodic tiles whose rows all lie inside the grid and
+// whose width is whole qualify: the tensor copy of the plane zero-fills those chunks in the
+// slot, a second tensor copy of the wrapped column fills the side array alongside it on the
+// same barrier, and the consumer lanes at the tile's ends read the side array instead -- the
+// producer never touches the plane again.  Producer and consumers evaluate the same rule.
+__device__ __forceinline__ int ring_side_bits(bool use_side, int x0, int y0, int nx, int ny,
+                                              int TX, int TY, int R, int A) {
+    if (!use_side || y0 < R || y0 + TY + R > ny || nx < A) return 0;
+    const bool right = x0 + TX + A > nx;
+    if (right && x0 + TX != nx) return 0;  // a partial tile: the wrap lands inside the tile
+    return (x0 == 0 ? 1 : 0) | (right ? 2 : 0);
+}
 
 // The producer warp: fills slot k with plane k of the CTA's sequence once every consumer warp
 // has released plane k - ns, then exits after the copies still in flight have landed.
 //  mode 2, TMA: lane 0 announces the bytes and issues one 3D tensor copy per field; the
 //    hardware zero-fills everything outside the grid (Dirichlet ghosts).
-//  mode 4, TMA + patches: a tile into which a periodic grid wraps takes the same tensor
+//  mode 5, TMA + side chunks: a periodic tile that wraps only in x (ring_side_bits) takes the
+//    same tensor copy plus one copy of each wrapped 16-byte column into the slot's side
+//    arrays, all on the full barrier, like mode 2.
+//  mode 4, TMA + patches: any other tile into which a periodic grid wraps takes the same tensor
 //    copies, on the slot's "tma" barrier; once they have landed (the producer turns to it
 //    whenever no slot is free), the lanes copy the wrapped 16-byte chunks (whole rows above
 //    or below the grid, single chunks left or right of it) over the zero fill with cp.async
@@ -190,9 +227,11 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
         const int nrow_oob = lo_row + (rows - hi_row);
         const int nwc = lo_chk + (CPR - hi_chk);
         const int npatch = nrow_oob * CPR + (hi_row - lo_row) * nwc;
+        const int sbits = ring_side_bits(src.use_side, q.x0, q.y0, nx, ny, TX, wk.TY, R, A);
         int mode;
         if (!src.use_tma) mode = src.aligned ? 1 : 0;
         else if (!periodic || npatch == 0) mode = 2;
+        else if (sbits != 0) mode = 5;
         else if (npatch <= kMaxPatches && hi_row >= lo_row) mode = 4;
         else mode = 3;
         if (mode == 4) {
@@ -243,17 +282,28 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
             const int gz = (NDIM == 3) ? wrap_or_flag(zi, src.nz, periodic, zok) : 0;
             const uint32_t bar = g.full_u32 + 8u * pos.slot;
             const uint32_t sbase = g.base_u32 + (uint32_t)pos.slot * g.slot_bytes;
-            if (mode == 2 || mode == 4) {
+            if (mode == 2 || mode == 4 || mode == 5) {
                 if (lane == 0) {
                     fence_proxy_async_shared();  // consumers' reads of this slot come first
-                    const uint32_t tb = mode == 2 ? bar : g.tma_u32 + 8u * pos.slot;
-                    mbar_arrive_expect_tx(tb, NF * plane_bytes);
+                    const uint32_t tb = mode == 4 ? g.tma_u32 + 8u * pos.slot : bar;
+                    const uint32_t side_bytes =
+                        mode == 5 ? (uint32_t)(__popc(sbits) * rows * 16) : 0u;
+                    mbar_arrive_expect_tx(tb, NF * plane_bytes + side_bytes);
                     const int zc = (NDIM == 3) ? (periodic ? gz : zi) : 0;
 #pragma unroll
                     for (int f = 0; f < NF; ++f)
                         tma_load_3d(sbase + f * g.field_bytes, &src.tmap[f], q.x0 - A, q.y0 - R,
                                     zc, tb);
-                } else if (mode == 2) {
+                    if (mode == 5) {
+                        // the wrapped columns: left chunk from x = nx - A, right one from x = 0
+                        const uint32_t side = sbase + g.side_off;
+                        if (sbits & 1)
+                            tma_load_3d(side, src.side_tmap, nx - A, q.y0 - R, zc, tb);
+                        if (sbits & 2)
+                            tma_load_3d(side + RingLayout::side_half(rows), src.side_tmap, 0,
+                                        q.y0 - R, zc, tb);
+                    }
+                } else if (mode != 4) {
                     mbar_arrive(bar);
                 }
                 if (mode == 4) ++unpub;
@@ -343,25 +393,38 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
                 issue(zi);
             }
         } else {
-            // Patched planes: issue whenever a slot is free; otherwise publish the oldest
-            // issued plane (waiting for its tensor copy), otherwise wait for a slot.  So the
-            // publishing of a plane never waits for a slot (which would wait for consumers,
-            // which wait for published planes).
+            // Patched planes: issue whenever a slot is free, publish the oldest issued plane
+            // as soon as its tensor copies have landed, and otherwise doze briefly and look
+            // again -- never block on one of the two, so a slot freed while a copy is in
+            // flight is refilled at once, and publishing never waits for a slot (which would
+            // wait for consumers, which wait for published planes).  The idle time is bounded.
             int zi = q.zs, zp = q.zs;  // next plane to issue / to publish
+            unsigned int idle = 0;
+            unsigned long long t0 = 0;
             while (zp < q.zl) {
                 if (zi < q.zl &&
                     __all_sync(0xffffffffu,
                                mbar_test_wait(g.empty_u32 + 8u * pos.slot, pos.phase ^ 1u))) {
                     issue(zi++);
-                } else if (zp < zi) {
+                    idle = 0;
+                } else if (zp < zi &&
+                           __all_sync(0xffffffffu, mbar_test_wait(g.tma_u32 + 8u * pslot,
+                                                                  (tbits >> pslot) & 1u))) {
                     if (!publish(zp)) {
                         ok = false;
                         break;
                     }
                     ++zp;
-                } else if (!wait_all(g.empty_u32 + 8u * pos.slot, pos.phase ^ 1u)) {
-                    ok = false;
-                    break;
+                    idle = 0;
+                } else {
+                    if (idle++ == 0) t0 = globaltimer_ns();
+                    else if ((idle & 63u) == 0 &&
+                             __any_sync(0xffffffffu, *g.abort_flag != 0 ||
+                                                         globaltimer_ns() - t0 > kRingWaitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(40);
                 }
             }
         }

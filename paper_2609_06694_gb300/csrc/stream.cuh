@@ -9,8 +9,10 @@
 //    the host to fill the shared memory the resident CTAs leave) filled with input planes --
 //    tile plus an R-row halo in y and one 16-byte chunk of halo in x -- by 3D TMA tensor
 //    copies (hardware zero fill = Dirichlet ghosts; the chunks a periodic grid wraps into an
-//    edge tile are patched over the fill once the copy has landed).  Slots are handed over by
-//    "full"/"empty" mbarriers, never by a CTA-wide barrier; every wait is bounded.
+//    edge tile are patched over the fill once the copy has landed -- except the x halo chunks
+//    of tiles at the x ends of the grid, which a second tensor copy puts into side arrays of
+//    the slot, read by the lanes at the tile's ends).  Slots are handed over by "full"/"empty"
+//    mbarriers, never by a CTA-wide barrier; every wait is bounded.
 //  * Each plane contributes to the 2R+1 output planes it touches: every thread keeps, per owned
 //    cell, a queue of 2R+1 FP32 partial sums in registers, adds the 2D slice of the offset set
 //    that lies at each dz, and writes the oldest sum once the plane R above it has arrived.
@@ -35,22 +37,6 @@ __device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int
 }
 template <int N, typename F> __device__ __forceinline__ void static_for(F &&f) {
     static_for_impl<N>(f, std::make_integer_sequence<int, N>{});
-}
-
-// Calls f(integral_constant<k>) for the runtime value ph in [0, P), P <= 9, via a switch.
-template <int P, typename F> __device__ __forceinline__ void phase_switch(int ph, F &&f) {
-    static_assert(P <= 9, "phase_switch handles up to 9 phases");
-    switch (ph) {
-#define GST_PHASE_CASE(k)                                                 \
-    case k:                                                               \
-        if constexpr (k < P) f(std::integral_constant<int, k>{});         \
-        break;
-        GST_PHASE_CASE(0) GST_PHASE_CASE(1) GST_PHASE_CASE(2) GST_PHASE_CASE(3)
-        GST_PHASE_CASE(4) GST_PHASE_CASE(5) GST_PHASE_CASE(6) GST_PHASE_CASE(7)
-        GST_PHASE_CASE(8)
-#undef GST_PHASE_CASE
-    default: break;
-    }
 }
 
 // a[v] = fma(c, w[v], a[v]) for v < N.  PAIRED issues the packed two-lane FP32 FMA of sm_100+
@@ -142,7 +128,8 @@ template <int NPTS> struct ConstCoeffs {
 };
 
 template <typename T> struct StreamParams {
-    CUtensorMap tmap;   // 3D (x, y, z) map of `in`, box (128 + 2A, TY + 2R, 1)
+    CUtensorMap tmap;       // 3D (x, y, z) map of `in`, box (128 + 2A, TY + 2R, 1)
+    CUtensorMap side_tmap;  // the same grid, box (A, TY + 2R, 1) (use_side only)
     const T *in;
     T *out;
     int nx, ny, nz;     // 2D grids: nz = 1
@@ -151,6 +138,7 @@ template <typename T> struct StreamParams {
     int tiles_x, tiles_y;
     int work;           // planes per CTA (flattened tile x z sequence)
     int use_tma;        // 1 = tensor-map loads (tmap describes `in`)
+    int use_side;       // 1 = x-wrapped halo chunks of edge tiles by side copies (periodic)
     int nstage;         // ring slots, 2 .. kMaxStages
     int z_lo, z_cnt;    // output planes [z_lo, z_lo + z_cnt) (3D; 0, 1 for 2D)
     int *err;           // device error word (may be null)
@@ -194,10 +182,8 @@ struct PlainStoreEpi {
 
 // How the partial-sum queue is indexed:
 //  kQueueUnrolled : the z loop is unrolled by 2R+1 so every queue index is a constant;
-//  kQueueRotate   : the queue is shifted by one entry after every plane (large stencils);
-//  kQueueStarSplit: stars only -- the in-plane cross goes to a temporary, and a switch on
-//                   the plane's phase adds it and the 2R single-point z terms to the queue.
-enum QueueMode : int { kQueueUnrolled = 0, kQueueRotate = 1, kQueueStarSplit = 2 };
+//  kQueueRotate   : the queue is shifted by one entry after every plane (large stencils).
+enum QueueMode : int { kQueueUnrolled = 0, kQueueRotate = 1 };
 
 template <typename T, int NDIM, int SHAPE, int R, int VY, int QMODE>
 struct StreamKernel {
@@ -211,35 +197,47 @@ struct StreamKernel {
     using OT = OffsetTable<NDIM, SHAPE, R>;
     static constexpr int NPTS = OT::count;
     static constexpr bool CREG = NPTS <= 32;         // coefficients held in registers
-    // Consumer threads per CTA: with the producer warp a CTA is then at most 8 (16) warps,
-    // two (four) per SM sub-partition, which keeps the register cap at 255 (128).  Wide-halo
-    // 3D stars with one row per thread may take the taller tiles.
-    static constexpr int MAX_THREADS = (NDIM == 3 && SHAPE == kStar && R >= 3 && VY == 1) ? 480 : 224;
+    // Consumer threads per CTA: with the producer warp a CTA is then at most 8 warps, two per
+    // SM sub-partition, which keeps the register cap at 255.  Wide-halo 3D stars with one row
+    // per thread may take 8 consumer warps: their 288-thread bound leaves the compiler room
+    // for the 72 registers of three resident CTAs (a 512-thread bound made it squeeze to 64
+    // registers and spill).
+    static constexpr int MAX_THREADS =
+        (NDIM == 3 && SHAPE == kStar && R >= 3 && VY == 1) ? 256 : 224;
     static_assert(R <= A, "x halo must fit in one 16-byte chunk");
-    static_assert(QMODE != kQueueStarSplit || SHAPE == kStar, "split mode is for stars");
 
     // needed |dx| for window row wr (union over the thread's rows and every dz); -1 = unused
-    __host__ __device__ static constexpr int row_m(int wr, bool inplane_only) {
+    __host__ __device__ static constexpr int row_m(int wr) {
         int m = -1;
         for (int vy = 0; vy < VY; ++vy) {
             int dy = wr - R - vy;
             if (dy < -R || dy > R) continue;
-            int v = inplane_only ? OT::tab.mdx[R][dy + R] : OT::max_dx_any(dy);
+            int v = OT::max_dx_any(dy);
             if (v > m) m = v;
         }
         return m;
     }
 
-    // ring slot size (one field, rounded to 128 bytes) and the shared memory of a CTA
-    __host__ __device__ static constexpr size_t slot_bytes(int by) {
+    // ring slot: one field (rounded to 128 bytes), then the side arrays of kernels that take
+    // them; shared memory of a CTA
+    __host__ __device__ static constexpr uint32_t field_bytes(int by) {
         return RingLayout::field_size(PITCH, by * VY + 2 * R, (int)sizeof(T));
     }
-    static size_t smem_bytes(int by, int nstage) {
-        return RingLayout::bytes((uint32_t)slot_bytes(by), nstage);
+    __host__ __device__ static constexpr uint32_t side_bytes(int by, bool side) {
+        return side ? RingLayout::side_size(by * VY + 2 * R) : 0u;
+    }
+    __host__ __device__ static constexpr size_t slot_bytes(int by, bool side) {
+        return field_bytes(by) + side_bytes(by, side);
+    }
+    static size_t smem_bytes(int by, bool side, int nstage) {
+        return RingLayout::bytes((uint32_t)slot_bytes(by, side), nstage);
     }
 };
 
-template <typename T, int NDIM, int SHAPE, int R, int VY, int QMODE, class EPI = PlainStoreEpi>
+// SIDE: the launch may take x halo chunks through side arrays (periodic grids with a side
+// tensor map); a kernel without SIDE has no side arrays and reads every halo chunk in place.
+template <typename T, int NDIM, int SHAPE, int R, int VY, int QMODE, class EPI = PlainStoreEpi,
+          bool SIDE = false>
 __global__ void __launch_bounds__(
     (StreamKernel<T, NDIM, SHAPE, R, VY, QMODE>::MAX_THREADS) + 32)
     stream_sweep_kernel(const __grid_constant__ StreamParams<T> p,
@@ -258,7 +256,7 @@ __global__ void __launch_bounds__(
     const int TY = by * VY;
     const int rows = TY + 2 * R;
     Ring g;
-    g.setup(smem_raw, (uint32_t)K::slot_bytes(by), 1, p.nstage);
+    g.setup(smem_raw, K::field_bytes(by), 1, p.nstage, K::side_bytes(by, SIDE));
     if (tid == 0) g.init(ncons / 32);
     __syncthreads();  // the only CTA-wide barrier: from here on the warps meet at mbarriers
 
@@ -271,6 +269,8 @@ __global__ void __launch_bounds__(
         // producer warp
         RingSource<T, 1> src;
         src.tmap = &p.tmap;
+        src.side_tmap = &p.side_tmap;
+        src.use_side = SIDE && p.use_side != 0;
         src.field = &p.in;
         src.nx = nx;
         src.ny = ny;
@@ -296,16 +296,35 @@ __global__ void __launch_bounds__(
         else return cf.c[idx];
     };
     const int thr_off = (ty * VY) * PITCH + A + tx * VX;  // element offset of the thread's base
+    // side arrays, in elements from a slot's side base: the thread's first row in the left
+    // array, shifted so that window position -A is chunk element 0; in the right array,
+    // shifted so that window position VX is chunk element 0
+    const int sl_off = (ty * VY) * A + A;
+    const int sr_off = (int)(RingLayout::side_half(rows) / sizeof(T)) + (ty * VY) * A - VX;
     bool failed = false;
 
     RingPos pos;  // ring position of the next plane
+    // Where window positions < 0 (the chunk left of the thread's cells) and >= VX (the chunk
+    // right of them) of window row wr come from: lb + wr * ls and rb + wr * rs -- the plane's
+    // own row (stride PITCH), or for the lanes at the ends of an x-edge tile a side array
+    // (stride A).  Set per piece (strides) and per plane (bases).
+    int ls = PITCH, rs = PITCH;
+    bool use_l = false, use_r = false;
+    const T *lb = nullptr, *rb = nullptr;
     // wait for the next plane to land; null once a bounded wait has given up
     auto begin_plane = [&]() -> const T * {
         if (!g.wait_full(pos.slot, pos.phase)) {
             failed = true;  // the whole warp
             return nullptr;
         }
-        return reinterpret_cast<const T *>(g.slot_ptr(pos.slot)) + thr_off;
+        const unsigned char *sp = g.slot_ptr(pos.slot);
+        const T *tb = reinterpret_cast<const T *>(sp) + thr_off;
+        if constexpr (SIDE) {
+            const T *side = reinterpret_cast<const T *>(sp + g.side_off);
+            lb = use_l ? side + sl_off : tb;
+            rb = use_r ? side + sr_off : tb;
+        }
+        return tb;
     };
     // this warp has read the slot: release it to the producer and move on
     auto end_plane = [&]() {
@@ -326,6 +345,16 @@ __global__ void __launch_bounds__(
     #pragma unroll
                 for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] = 0.0f;
 
+        // the lanes at the ends of an x-edge tile read their wrapped halo chunk from a side array
+        if constexpr (SIDE) {
+            const int sbits =
+                ring_side_bits(p.use_side != 0, q.x0, q.y0, nx, ny, TX, TY, R, A);
+            use_l = (sbits & 1) && tx == 0;
+            use_r = (sbits & 2) && tx == K::BX - 1;
+            ls = use_l ? A : PITCH;
+            rs = use_r ? A : PITCH;
+        }
+
         // output addressing, hoisted
         const int ox = q.x0 + tx * VX;
         const int oy = q.y0 + ty * VY;
@@ -342,35 +371,38 @@ __global__ void __launch_bounds__(
             EPI::template apply<T, VY, VX>(p, ep, zo, oy, ox, xfull, vy_valid, eregs, vals);
         };
 
-        // add the in-plane slice(s) of the plane at `tb` to the queue; JOF(dz) = queue index of
-        // output (zi - dz).  INPLANE_ONLY restricts to dz = 0 and writes into `tmp` instead.
-        auto accumulate = [&](const T *tb, auto jof, auto inplane_only_c, float (&tmp)[VY][VX]) {
-            constexpr bool IPO = decltype(inplane_only_c)::value;
+        // add the in-plane slices of the plane at `tb` to the queue; JOF(dz) = queue index of
+        // output (zi - dz)
+        auto accumulate = [&](const T *tb, auto jof) {
             static_for<VY + 2 * R>([&](auto wr_c) {
                 constexpr int wr = decltype(wr_c)::value;
-                constexpr int m = K::row_m(wr, IPO);
+                constexpr int m = K::row_m(wr);
                 if constexpr (m >= 0) {
                     float win[VX + 2 * R];
-                    load_span<T, -m, VX + m, -R>(tb + wr * PITCH, win);
+                    const T *crow = tb + wr * PITCH;
+                    if constexpr (SIDE && m > 0) {
+                        load_span<T, -m, 0, -R>(lb + wr * ls, win);
+                        load_span<T, 0, VX, -R>(crow, win);
+                        load_span<T, VX, VX + m, -R>(rb + wr * rs, win);
+                    } else {
+                        load_span<T, -m, VX + m, -R>(crow, win);
+                    }
                     static_for<VY>([&](auto vy_c) {
                         constexpr int vy = decltype(vy_c)::value;
                         constexpr int dy = wr - R - vy;
                         if constexpr (dy >= -R && dy <= R) {
                             static_for<P>([&](auto dzi_c) {
                                 constexpr int dz = decltype(dzi_c)::value - RZ;
-                                if constexpr (!IPO || dz == 0) {
-                                    constexpr int j =
-                                        decltype(jof(std::integral_constant<int, dz>{}))::value;
-                                    static_for<2 * R + 1>([&](auto dxi_c) {
-                                        constexpr int dx = decltype(dxi_c)::value - R;
-                                        constexpr int idx = K::OT::index(dz, dy, dx);
-                                        if constexpr (idx >= 0) {
-                                            const float c = coef(std::integral_constant<int, idx>{});
-                                            float *dst = IPO ? tmp[vy] : acc[j][vy];
-                                            fma_n<VX, dx % 2 == 0>(c, win + (dx + R), dst);
-                                        }
-                                    });
-                                }
+                                constexpr int j =
+                                    decltype(jof(std::integral_constant<int, dz>{}))::value;
+                                static_for<2 * R + 1>([&](auto dxi_c) {
+                                    constexpr int dx = decltype(dxi_c)::value - R;
+                                    constexpr int idx = K::OT::index(dz, dy, dx);
+                                    if constexpr (idx >= 0) {
+                                        const float c = coef(std::integral_constant<int, idx>{});
+                                        fma_n<VX, dx % 2 == 0>(c, win + (dx + R), acc[j][vy]);
+                                    }
+                                });
                             });
                         }
                     });
@@ -387,7 +419,6 @@ __global__ void __launch_bounds__(
 
 
         int zi = q.zs;
-        float dummy[VY][VX];
         if constexpr (QMODE == kQueueUnrolled) {
             bool done = false;
             while (!done) {
@@ -407,7 +438,7 @@ __global__ void __launch_bounds__(
                     accumulate(tb, [](auto dz_c) {
                         constexpr int dz = decltype(dz_c)::value;
                         return std::integral_constant<int, imod_c(ph - dz, P)>{};
-                    }, std::false_type{}, dummy);
+                    });
                     end_plane();
                     constexpr int jo = imod_c(ph - RZ, P);
                     store_output(zi - RZ, acc[jo]);
@@ -423,7 +454,7 @@ __global__ void __launch_bounds__(
                 accumulate(tb, [](auto dz_c) {
                     constexpr int dz = decltype(dz_c)::value;
                     return std::integral_constant<int, RZ - dz>{};
-                }, std::false_type{}, dummy);
+                });
                 end_plane();
                 store_output(zi - RZ, acc[0]);
     #pragma unroll
@@ -433,50 +464,6 @@ __global__ void __launch_bounds__(
     #pragma unroll
                         for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] = acc[j + 1][vy][vx];
                 zero_slot(acc[P - 1]);
-            }
-        } else {
-            // star split: in-plane cross into tmp, then a phase switch for the z line
-            int ph = 0;
-            for (; zi < zl; ++zi) {
-                prefetch_output(zi - RZ);
-                const T *tb = begin_plane();
-                if (!tb) break;
-                float tmp[VY][VX];
-                zero_slot(tmp);
-                accumulate(tb, [](auto) { return std::integral_constant<int, 0>{}; },
-                           std::true_type{}, tmp);
-                // centre values of this plane (the z-line terms read them)
-                float ctr[VY][VX];
-    #pragma unroll
-                for (int vy = 0; vy < VY; ++vy) {
-                    float wv[VX];
-                    load_span<T, 0, VX, 0>(tb + (vy + R) * PITCH, wv);
-    #pragma unroll
-                    for (int vx = 0; vx < VX; ++vx) ctr[vy][vx] = wv[vx];
-                }
-                end_plane();
-                phase_switch<P>(ph, [&](auto ph_c) {
-                    constexpr int PH = decltype(ph_c)::value;
-                    static_for<P>([&](auto dzi_c) {
-                        constexpr int dz = decltype(dzi_c)::value - RZ;
-                        constexpr int j = imod_c(PH - dz, P);
-    #pragma unroll
-                        for (int vy = 0; vy < VY; ++vy) {
-                            if constexpr (dz == 0) {
-    #pragma unroll
-                                for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] += tmp[vy][vx];
-                            } else {
-                                fma_n<VX, true>(
-                                    coef(std::integral_constant<int, K::OT::index(dz, 0, 0)>{}),
-                                    ctr[vy], acc[j][vy]);
-                            }
-                        }
-                    });
-                    constexpr int jo = imod_c(PH - RZ, P);
-                    store_output(zi - RZ, acc[jo]);
-                    zero_slot(acc[jo]);
-                });
-                ph = (ph + 1 == P) ? 0 : ph + 1;
             }
         }
     }  // pieces

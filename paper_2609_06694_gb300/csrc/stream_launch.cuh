@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 #include "ring_launch.cuh"
@@ -9,65 +10,26 @@
 
 namespace gst {
 
-// Queue mode: 3D stars split off their in-plane cross; other small stencils unroll the z loop
-// by 2R+1 while the unrolled body stays small; larger ones rotate their partial-sum queue.
+// Queue mode: the z loop is unrolled by 2R+1 while the unrolled body stays small; larger
+// stencils rotate their partial-sum queue.
 constexpr int stream_queue_mode(int ndim, int shape, int r, int vx, int vy) {
-    if (ndim == 3 && shape == kStar) return kQueueStarSplit;
     if (ndim == 2 || shape_count(ndim, shape, r) * vx * vy * (2 * r + 1) <= 2000)
         return kQueueUnrolled;
     return kQueueRotate;
 }
 
-// One launch of the streaming kernel; EPI decides what happens to finished outputs (the plain
-// store, or a fused update with its own parameter block `ep`).
-template <typename T, int NDIM, int SHAPE, int R, int VY, class EPI = PlainStoreEpi>
-int launch_stream_t(const StreamLaunch &L,
-                    const typename EPI::Params &ep = typename EPI::Params{}) {
-    constexpr int VX = 16 / (int)sizeof(T);
-    constexpr int NPTS = OffsetTable<NDIM, SHAPE, R>::count;
-    constexpr int QM = stream_queue_mode(NDIM, SHAPE, R, VX, VY);
+// The launch proper: ring depth, shared memory, work split, grid.
+template <typename T, int NDIM, int SHAPE, int R, int VY, int QM, class EPI, bool SIDE>
+int launch_stream_go(const StreamLaunch &L, StreamParams<T> &p,
+                     const ConstCoeffs<OffsetTable<NDIM, SHAPE, R>::count> &cf,
+                     const typename EPI::Params &ep) {
     using K = StreamKernel<T, NDIM, SHAPE, R, VY, QM>;
-    auto kern = stream_sweep_kernel<T, NDIM, SHAPE, R, VY, QM, EPI>;
-
+    auto kern = stream_sweep_kernel<T, NDIM, SHAPE, R, VY, QM, EPI, SIDE>;
     const int by = L.block_y;
-    if (L.block_x != K::BX || by < 1 || K::BX * by > K::MAX_THREADS || (K::BX * by) % 32 != 0)
-        return -1;
-    const int TX = K::TX, TY = by * VY;
-    const int64_t nx = L.nx, ny = L.ny, nz = NDIM == 3 ? L.nz : 1;
-    if (nx * ny > (int64_t)INT32_MAX - 4 * TX) return -2;
-
-    StreamParams<T> p;
-    p.in = static_cast<const T *>(L.in);
-    p.out = static_cast<T *>(L.out);
-    p.nx = (int)nx;
-    p.ny = (int)ny;
-    p.nz = (int)nz;
-    p.periodic = L.periodic;
-    p.tiles_x = (int)((nx + TX - 1) / TX);
-    p.tiles_y = (int)((ny + TY - 1) / TY);
-    p.z_lo = NDIM == 3 ? (int)std::max<int64_t>(0, L.z_lo) : 0;
-    const int64_t z_hi = NDIM == 3 ? (L.z_hi < 0 ? nz : std::min<int64_t>(L.z_hi, nz)) : 1;
-    if (z_hi <= p.z_lo) return 0;  // nothing to sweep
-    p.z_cnt = (int)(z_hi - p.z_lo);
-    const bool ptr_ok = ((uintptr_t)L.in % 16 == 0) && ((uintptr_t)L.out % 16 == 0);
-    p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
-    p.err = L.err;
-
-    // Tensor-map (TMA) loads when rows are 16-byte aligned and the box fits the TMA limits
-    // (the chunks a periodic grid wraps into an edge tile are patched inside the kernel).
-    const int rows = TY + 2 * R;
-    p.use_tma = (p.aligned && L.use_tma != 0 &&
-                 encode_plane_map<T>(&p.tmap, L.in, nx, ny, nz, K::PITCH, rows))
-                    ? 1
-                    : 0;
-
-    ConstCoeffs<NPTS> cf;
-    for (int i = 0; i < NPTS; ++i) cf.c[i] = L.coeffs[i];
-
     const int threads = K::BX * by + 32;  // consumers + the producer warp
     p.nstage = ring_stages(L.stages, NDIM, reinterpret_cast<const void *>(kern), threads,
-                           K::slot_bytes(by));
-    const size_t smem = K::smem_bytes(by, p.nstage);
+                           K::slot_bytes(by, SIDE));
+    const size_t smem = K::smem_bytes(by, SIDE, p.nstage);
     static size_t smem_set = 0;  // per instantiation
     if (smem > 48 * 1024 && smem > smem_set) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -96,6 +58,64 @@ int launch_stream_t(const StreamLaunch &L,
     kern<<<(unsigned)nblocks, dim3(K::BX, by + 32 / K::BX), smem, L.stream>>>(p, cf, ep);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
+}
+
+// One launch of the streaming kernel; EPI decides what happens to finished outputs (the plain
+// store, or a fused update with its own parameter block `ep`).
+template <typename T, int NDIM, int SHAPE, int R, int VY, class EPI = PlainStoreEpi>
+int launch_stream_t(const StreamLaunch &L,
+                    const typename EPI::Params &ep = typename EPI::Params{}) {
+    constexpr int VX = 16 / (int)sizeof(T);
+    constexpr int NPTS = OffsetTable<NDIM, SHAPE, R>::count;
+    constexpr int QM = stream_queue_mode(NDIM, SHAPE, R, VX, VY);
+    using K = StreamKernel<T, NDIM, SHAPE, R, VY, QM>;
+
+    const int by = L.block_y;
+    if (L.block_x != K::BX || by < 1 || K::BX * by > K::MAX_THREADS || (K::BX * by) % 32 != 0)
+        return -1;
+    const int TX = K::TX, TY = by * VY;
+    const int64_t nx = L.nx, ny = L.ny, nz = NDIM == 3 ? L.nz : 1;
+    if (nx * ny > (int64_t)INT32_MAX - 4 * TX) return -2;
+
+    StreamParams<T> p{};
+    p.in = static_cast<const T *>(L.in);
+    p.out = static_cast<T *>(L.out);
+    p.nx = (int)nx;
+    p.ny = (int)ny;
+    p.nz = (int)nz;
+    p.periodic = L.periodic;
+    p.tiles_x = (int)((nx + TX - 1) / TX);
+    p.tiles_y = (int)((ny + TY - 1) / TY);
+    p.z_lo = NDIM == 3 ? (int)std::max<int64_t>(0, L.z_lo) : 0;
+    const int64_t z_hi = NDIM == 3 ? (L.z_hi < 0 ? nz : std::min<int64_t>(L.z_hi, nz)) : 1;
+    if (z_hi <= p.z_lo) return 0;  // nothing to sweep
+    p.z_cnt = (int)(z_hi - p.z_lo);
+    const bool ptr_ok = ((uintptr_t)L.in % 16 == 0) && ((uintptr_t)L.out % 16 == 0);
+    p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
+    p.err = L.err;
+
+    // Tensor-map (TMA) loads when rows are 16-byte aligned and the box fits the TMA limits
+    // (the chunks a periodic grid wraps into an edge tile are filled inside the kernel).
+    const int rows = TY + 2 * R;
+    p.use_tma = (p.aligned && L.use_tma != 0 &&
+                 encode_plane_map<T>(&p.tmap, L.in, nx, ny, nz, K::PITCH, rows))
+                    ? 1
+                    : 0;
+    // periodic grids: the wrapped x halo chunks of edge tiles by a second map (one chunk wide)
+    p.use_side = (p.use_tma && L.periodic &&
+                  encode_plane_map<T>(&p.side_tmap, L.in, nx, ny, nz, K::A, rows))
+                     ? 1
+                     : 0;
+
+    ConstCoeffs<NPTS> cf;
+    for (int i = 0; i < NPTS; ++i) cf.c[i] = L.coeffs[i];
+
+    // the side-array kernel only where side chunks may be taken (plain periodic sweeps)
+    if constexpr (std::is_same<EPI, PlainStoreEpi>::value) {
+        if (p.use_side) return launch_stream_go<T, NDIM, SHAPE, R, VY, QM, EPI, true>(L, p, cf, ep);
+    }
+    p.use_side = 0;
+    return launch_stream_go<T, NDIM, SHAPE, R, VY, QM, EPI, false>(L, p, cf, ep);
 }
 
 template <typename T, int NDIM, int SHAPE, int R> int launch_stream_vy(const StreamLaunch &L) {

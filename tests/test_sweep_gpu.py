@@ -104,9 +104,9 @@ def test_stream_variants_agree(shape, vec_y, blocks, stages):
 @pytest.mark.parametrize("stages", [2, 16])
 def test_stream_ring_depth_radius4(bc, stages):
     # wide stars on a grid that is several tiles wide and tall with ragged edges, with the
-    # shallowest and the deepest ring, up to the 480-thread consumer tile
+    # shallowest and the deepest ring, up to the 256-thread consumer tile
     dims = (40, 70, 300)
-    for r, by in ((4, 4), (4, 8), (4, 15), (3, 15)):
+    for r, by in ((4, 4), (4, 8), (4, 7), (3, 8)):
         offs = oracle.offsets(3, "star", r)
         c = seeded_weights(43, len(offs))
         plan = gs.stencil_plan(3, dims, "star", r, "const", c, "f32", bc)
@@ -120,14 +120,42 @@ def test_stream_ring_depth_radius4(bc, stages):
 @pytest.mark.parametrize("shape,r", [("star", 4), ("box", 1), ("star", 2)])
 def test_periodic_whole_tile_widths(dtype, shape, r):
     # periodic grids whose width is a whole number of 128-cell tiles: the first and last tile
-    # columns wrap exactly one 16-byte chunk per row, patched over the tensor copy's zero
-    # fill; a single tile column is patched on both sides at once
+    # columns wrap exactly one 16-byte chunk per row, which a second tensor copy puts into the
+    # slot's side arrays (tiles whose rows wrap too are patched instead); a single tile
+    # column takes both side chunks at once
     for dims in ((20, 40, 256), (9, 33, 128)):
         offs = oracle.offsets(3, shape, r)
         c = seeded_weights(47, len(offs))
         plan = gs.stencil_plan(3, dims, shape, r, "const", c, dtype, "periodic")
         x, x64 = make_input(48, dims, dtype)
         assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, "periodic")) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("shape,r,block_y,vec_y", [("star", 4, 8, 1), ("star", 4, 7, 2),
+                                                   ("star", 4, 4, 2), ("star", 2, 3, 2),
+                                                   ("box", 1, 4, 2), ("box", 1, 7, 1),
+                                                   ("diamond", 2, 5, 1)])
+def test_periodic_side_chunks(dtype, shape, r, block_y, vec_y):
+    # tall periodic grids of whole tile columns: most tiles of the first and last column take
+    # their x halo from the side arrays, the tiles at the y ends are patched, for several tile
+    # heights; and one 2D grid
+    cases = [(3, (11, 70, 256)), (3, (6, 50, 128))]
+    if vec_y == 1:
+        cases.append((2, (90, 256)))
+    for ndim, dims in cases:
+        offs = oracle.offsets(ndim, shape, r)
+        c = seeded_weights(49, len(offs))
+        plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, dtype, "periodic")
+        # 16-bit rows of 128 cells take 16 threads: twice the rows keep whole warps
+        bx, by = (32, block_y) if dtype == "f32" else (16, 2 * block_y)
+        if ndim == 2:
+            by = min(by, 224 // bx)  # 2D tiles take at most 224 consumer threads
+        gs.stencil_plan_set_variant(plan, family=1, block_x=bx, block_y=by, vec_y=vec_y,
+                                    z_chunk=5, stages=0, fuse=1)
+        x, x64 = make_input(50, dims, dtype)
+        got = gpu_apply(plan, x)
+        assert relerr(got, oracle.sweep_const(x64, offs, c, "periodic")) < TOL[dtype], (ndim, dims)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
