@@ -42,20 +42,23 @@ template <int N, typename F> __device__ __forceinline__ void static_for(F &&f) {
 // a[v] = fma(c, w[v], a[v]) for v < N.  PAIRED issues the packed two-lane FP32 FMA of sm_100+
 // on (v, v+1) -- each lane rounds exactly like fmaf -- which halves the FMA instructions when
 // w[v], w[v+1] come from one aligned 8-byte pair of a vector load (an even x offset).
-template <int N, bool PAIRED>
+// FIRST: a[] holds no partial sum yet; the addend is +0 (the same bits as accumulating into
+// a zeroed entry), so the entry needs no zeroing and carries no dependency on its old value.
+template <int N, bool PAIRED, bool FIRST = false>
 __device__ __forceinline__ void fma_n(float c, const float *w, float *a) {
     if constexpr (PAIRED && N % 2 == 0) {
         const float2 c2 = make_float2(c, c);
 #pragma unroll
         for (int v = 0; v < N; v += 2) {
-            const float2 r =
-                __ffma2_rn(c2, make_float2(w[v], w[v + 1]), make_float2(a[v], a[v + 1]));
+            const float2 r = __ffma2_rn(c2, make_float2(w[v], w[v + 1]),
+                                        FIRST ? make_float2(0.0f, 0.0f)
+                                              : make_float2(a[v], a[v + 1]));
             a[v] = r.x;
             a[v + 1] = r.y;
         }
     } else {
 #pragma unroll
-        for (int v = 0; v < N; ++v) a[v] = fmaf(c, w[v], a[v]);
+        for (int v = 0; v < N; ++v) a[v] = fmaf(c, w[v], FIRST ? 0.0f : a[v]);
     }
 }
 
@@ -216,6 +219,20 @@ struct StreamKernel {
             if (v > m) m = v;
         }
         return m;
+    }
+
+    // The first term that output row vy receives from a plane at offset dz, in the order the
+    // accumulation visits them (window row wr, then dx): wr * 64 + dx + R, or -1.  A queue
+    // entry takes its first term from the plane at dz = -RZ.
+    __host__ __device__ static constexpr int first_term(int vy, int dz) {
+        for (int wr = 0; wr < VY + 2 * R; ++wr) {
+            if (row_m(wr) < 0) continue;
+            const int dy = wr - R - vy;
+            if (dy < -R || dy > R) continue;
+            for (int dx = -R; dx <= R; ++dx)
+                if (OT::index(dz, dy, dx) >= 0) return wr * 64 + dx + R;
+        }
+        return -1;
     }
 
     // ring slot: one field (rounded to 128 bytes), then the side arrays of kernels that take
@@ -400,7 +417,12 @@ __global__ void __launch_bounds__(
                                     constexpr int idx = K::OT::index(dz, dy, dx);
                                     if constexpr (idx >= 0) {
                                         const float c = coef(std::integral_constant<int, idx>{});
-                                        fma_n<VX, dx % 2 == 0>(c, win + (dx + R), acc[j][vy]);
+                                        // the entry's first term replaces its zeroing
+                                        constexpr bool FIRST =
+                                            dz == -RZ &&
+                                            K::first_term(vy, dz) == wr * 64 + dx + R;
+                                        fma_n<VX, dx % 2 == 0, FIRST>(c, win + (dx + R),
+                                                                      acc[j][vy]);
                                     }
                                 });
                             });
@@ -409,14 +431,6 @@ __global__ void __launch_bounds__(
                 }
             });
         };
-
-        auto zero_slot = [&](float (&a)[VY][VX]) {
-    #pragma unroll
-            for (int vy = 0; vy < VY; ++vy)
-    #pragma unroll
-                for (int vx = 0; vx < VX; ++vx) a[vy][vx] = 0.0f;
-        };
-
 
         int zi = q.zs;
         if constexpr (QMODE == kQueueUnrolled) {
@@ -442,7 +456,6 @@ __global__ void __launch_bounds__(
                     end_plane();
                     constexpr int jo = imod_c(ph - RZ, P);
                     store_output(zi - RZ, acc[jo]);
-                    zero_slot(acc[jo]);
                     ++zi;
                 });
             }
@@ -463,7 +476,6 @@ __global__ void __launch_bounds__(
                     for (int vy = 0; vy < VY; ++vy)
     #pragma unroll
                         for (int vx = 0; vx < VX; ++vx) acc[j][vy][vx] = acc[j + 1][vy][vx];
-                zero_slot(acc[P - 1]);
             }
         }
     }  // pieces
