@@ -208,16 +208,56 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
         load(zi);
         cp_async_commit();
     }
+    const bool row_ok = oy < ny;
+    // the coefficients output cell(s) of plane zo take for offset (dz, dy, dx): forward at the
+    // output cell, adjoint at the shifted source cell q - o (wrapped; a source outside a
+    // Dirichlet grid reads 0 from the tile anyway)
+    auto fetch_w = [&](int zo, int idx, int dz, int dy, int dx, float (&w)[VX]) {
+        if (!row_ok) {
+#pragma unroll
+            for (int i = 0; i < VX; ++i) w[i] = 0.0f;
+        } else if constexpr (!ADJ) {
+            load_cells<T, VX>(p.w[idx] + (size_t)zo * pstride + (size_t)oy * nx + ox, vec, nvalid,
+                              w);
+        } else {
+            bool ok = true;
+            const int gz = NDIM == 3 ? wrap_or_flag(zo - dz, nz, true, ok) : 0;
+            const int gy = wrap_or_flag(oy - dy, ny, true, ok);
+            const T *base = p.w[idx] + (size_t)gz * pstride + (size_t)gy * nx;
+#pragma unroll
+            for (int i = 0; i < VX; ++i) {
+                bool okx = true;
+                const int gx = wrap_or_flag(ox + i - dx, nx, true, okx);
+                w[i] = Storage<T>::to_float(__ldg(base + gx));
+            }
+        }
+    };
+    // Small offset sets fetch every coefficient of the plane into registers before the wait
+    // for the input planes, so the global loads are in flight during the wait and barrier.
+    constexpr bool PRE = OT::count * VX <= 32;
+    float wpre[PRE ? OT::count : 1][VX];
     for (int zo = z_begin; zo < z_end; ++zo) {
         // plane zo+RZ+1 goes into the slot freed by plane zo-RZ-1
         if (zo + RZ + 1 < z_end + RZ) load(zo + RZ + 1);
         cp_async_commit();
+        if constexpr (PRE) {
+            static_for<2 * RZ + 1>([&](auto dzi_c) {
+                static_for<2 * R + 1>([&](auto dyi_c) {
+                    static_for<2 * R + 1>([&](auto dxi_c) {
+                        constexpr int dz = decltype(dzi_c)::value - RZ;
+                        constexpr int dy = decltype(dyi_c)::value - R;
+                        constexpr int dx = decltype(dxi_c)::value - R;
+                        constexpr int idx = OT::index(dz, dy, dx);
+                        if constexpr (idx >= 0) fetch_w(zo, idx, dz, dy, dx, wpre[idx]);
+                    });
+                });
+            });
+        }
         cp_async_wait<1>();
         __syncthreads();
         float acc[VX];
 #pragma unroll
         for (int i = 0; i < VX; ++i) acc[i] = 0.0f;
-        const bool row_ok = oy < ny;
         static_for<2 * RZ + 1>([&](auto dzi_c) {
             constexpr int dz = decltype(dzi_c)::value - RZ;
             // forward reads plane zo+dz at rows/cols +d; the adjoint reads plane zo-dz at -d
@@ -236,31 +276,17 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
                         constexpr int idx = OT::index(dz, dy, dx);
                         if constexpr (idx >= 0) {
                             constexpr int rx = ADJ ? -dx : dx;
-                            float w[VX];
-                            if (!row_ok) {
+                            if constexpr (PRE) {
 #pragma unroll
-                                for (int i = 0; i < VX; ++i) w[i] = 0.0f;
-                            } else if constexpr (!ADJ) {
-                                load_cells<T, VX>(p.w[idx] + (size_t)zo * pstride +
-                                                      (size_t)oy * nx + ox,
-                                                  vec, nvalid, w);
+                                for (int i = 0; i < VX; ++i)
+                                    acc[i] = fmaf(wpre[idx][i], win[i + rx + R], acc[i]);
                             } else {
-                                // coefficient at the source cell q - o (wrapped; a source
-                                // outside a Dirichlet grid reads 0 from the tile anyway)
-                                bool ok = true;
-                                const int gz = NDIM == 3 ? wrap_or_flag(zo - dz, nz, true, ok) : 0;
-                                const int gy = wrap_or_flag(oy - dy, ny, true, ok);
-                                const T *base = p.w[idx] + (size_t)gz * pstride + (size_t)gy * nx;
+                                float w[VX];
+                                fetch_w(zo, idx, dz, dy, dx, w);
 #pragma unroll
-                                for (int i = 0; i < VX; ++i) {
-                                    bool okx = true;
-                                    const int gx = wrap_or_flag(ox + i - dx, nx, true, okx);
-                                    w[i] = Storage<T>::to_float(__ldg(base + gx));
-                                }
+                                for (int i = 0; i < VX; ++i)
+                                    acc[i] = fmaf(w[i], win[i + rx + R], acc[i]);
                             }
-#pragma unroll
-                            for (int i = 0; i < VX; ++i)
-                                acc[i] = fmaf(w[i], win[i + rx + R], acc[i]);
                         }
                     });
                 }
