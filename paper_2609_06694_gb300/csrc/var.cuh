@@ -232,15 +232,18 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
             }
         }
     };
-    // Small offset sets fetch every coefficient of the plane into registers before the wait
-    // for the input planes, so the global loads are in flight during the wait and barrier.
-    constexpr bool PRE = OT::count * VX <= 32;
-    float wpre[PRE ? OT::count : 1][VX];
+    // The first NPRE offsets (at most 32 values per thread) fetch their coefficients of the
+    // plane into registers before the wait for the input planes, so those global loads are in
+    // flight during the wait and barrier; the rest load where they are used.  The adjoint's
+    // gathers take part only when every offset fits (a partial set of gathered coefficients
+    // cost more in registers than it saved: 2x slower for the bf16 box).
+    constexpr int NPRE = OT::count * VX <= 32 ? OT::count : (ADJ ? 0 : 32 / VX);
+    float wpre[NPRE > 0 ? NPRE : 1][VX];
     for (int zo = z_begin; zo < z_end; ++zo) {
         // plane zo+RZ+1 goes into the slot freed by plane zo-RZ-1
         if (zo + RZ + 1 < z_end + RZ) load(zo + RZ + 1);
         cp_async_commit();
-        if constexpr (PRE) {
+        {
             static_for<2 * RZ + 1>([&](auto dzi_c) {
                 static_for<2 * R + 1>([&](auto dyi_c) {
                     static_for<2 * R + 1>([&](auto dxi_c) {
@@ -248,7 +251,8 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
                         constexpr int dy = decltype(dyi_c)::value - R;
                         constexpr int dx = decltype(dxi_c)::value - R;
                         constexpr int idx = OT::index(dz, dy, dx);
-                        if constexpr (idx >= 0) fetch_w(zo, idx, dz, dy, dx, wpre[idx]);
+                        if constexpr (idx >= 0 && idx < NPRE)
+                            fetch_w(zo, idx, dz, dy, dx, wpre[idx]);
                     });
                 });
             });
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
                         constexpr int idx = OT::index(dz, dy, dx);
                         if constexpr (idx >= 0) {
                             constexpr int rx = ADJ ? -dx : dx;
-                            if constexpr (PRE) {
+                            if constexpr (idx < NPRE) {
 #pragma unroll
                                 for (int i = 0; i < VX; ++i)
                                     acc[i] = fmaf(wpre[idx][i], win[i + rx + R], acc[i]);
