@@ -124,7 +124,8 @@ static bool lookup_map(const stencil_plan_s &p, stencil_variant *out) {
 int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
     if (p.kind != STENCIL_CONST) {
         // variable-coefficient kernels: 128-cell tiles, block_y rows of one output row per
-        // thread (at most 224 threads), z chunks of z_chunk planes (0 = whole columns)
+        // thread (at most 224 threads), z chunks of z_chunk planes (0: whole columns for the
+        // general sweeps, an equal share per resident CTA for div(k grad u))
         if (v.family != STENCIL_FAMILY_STREAM || v.vec_y != 1 || v.fuse != 1 ||
             v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
             v.block_x * v.block_y > 224 || (v.block_x * v.block_y) % 32 != 0 || v.z_chunk < 0)

@@ -125,9 +125,17 @@ template <typename T, int NDIM> int launch_divkgrad_nd(const VarLaunch &L) {
             return -4;
         smem_set = smem;
     }
-    // z chunks of z_chunk planes per CTA (whole columns when 0)
+    // z chunks of z_chunk planes per CTA; z_chunk == 0 sizes the grid to the CTAs that fit on
+    // the GPU at once and gives each an equal share of the (tile, z) planes (one wave, no tail)
     const int64_t total = (int64_t)p.tiles_x * p.tiles_y * nz;
-    const int64_t work = (NDIM == 3 && L.z_chunk > 0) ? L.z_chunk : nz;
+    int64_t work = nz;
+    if (NDIM == 3 && L.z_chunk > 0) {
+        work = L.z_chunk;
+    } else if (NDIM == 3) {
+        const int slots = resident_slots(reinterpret_cast<const void *>(kern), threads, smem);
+        if (slots < 1) return -2;
+        work = (total + slots - 1) / slots;
+    }
     p.work = (int)std::min<int64_t>(work, INT32_MAX);
     const int64_t nblocks = (total + p.work - 1) / p.work;
     if (nblocks > INT32_MAX) return -2;

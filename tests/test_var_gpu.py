@@ -80,6 +80,31 @@ def test_var_rejects_missing_arrays_and_unsupported_sets():
     assert e.value.code == -2  # 125 coefficient arrays: no kernel
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_divkgrad_work_splits(dtype, bc):
+    # one equal share of the (tile, z) planes per resident CTA (z_chunk 0: a CTA's planes span
+    # several tiles), short chunks that end mid-column, and several tile heights: every split
+    # gives the same bits and matches the oracle
+    dims = (23, 45, 264)
+    plan = gs.stencil_plan(3, dims, "star", 1, "divkgrad", None, dtype, bc)
+    k = inputs.to_storage(inputs.lognormal_k(3012, dims), dtype)
+    u = inputs.to_storage(inputs.uniform(3011, dims), dtype)
+    ref = oracle.divkgrad(inputs.stored_values(u), inputs.stored_values(k), bc)
+    base = gs.stencil_plan_get_variant(plan)
+    bx = base["block_x"]
+    first = None
+    for by, zc in ((4, 0), (2 if bx == 32 else 4, 0), (7 if bx == 32 else 14, 5), (1 if bx == 32 else 2, 9)):
+        gs.stencil_plan_set_variant(plan, **dict(base, block_y=by, z_chunk=zc, stages=0))
+        y = torch.empty_like(u, device="cuda")
+        gs.stencil_apply_var(plan, u.cuda(), [k.cuda()], y, 1)
+        assert gs.stencil_sync_status(plan) == 0
+        assert relerr(inputs.stored_values(y), ref) < TOL[dtype], (by, zc)
+        if first is None:
+            first = y.clone()
+        assert torch.equal(y, first), (by, zc)
+
+
 @pytest.mark.parametrize("ndim", [2, 3])
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
