@@ -219,7 +219,10 @@ static int launch_group(stencil_plan_s &p, const float *cf, const void *src, voi
     L.block_x = v.block_x;
     L.block_y = v.block_y;
     L.vec_y = v.vec_y;
-    L.z_chunk = v.z_chunk;
+    // a z sub-range (a slab of the host-buffer pipeline) holds too few planes to fill the GPU
+    // with the tuned chunks: every resident CTA takes an equal share of it instead
+    const bool slab = z_hi >= 0 && z_hi - z_lo < p.dims[0];
+    L.z_chunk = slab ? 0 : v.z_chunk;
     L.stages = v.stages;
     L.z_lo = z_lo;
     L.z_hi = z_hi;
