@@ -184,10 +184,10 @@ __device__ __forceinline__ int ring_side_bits(bool use_side, int x0, int y0, int
 //    same tensor copy plus one copy of each wrapped 16-byte column into the slot's side
 //    arrays, all on the full barrier, like mode 2.
 //  mode 4, TMA + patches: any other tile into which a periodic grid wraps takes the same tensor
-//    copies, on the slot's "tma" barrier; once they have landed (the producer turns to it
-//    whenever no slot is free), the lanes copy the wrapped 16-byte chunks (whole rows above
-//    or below the grid, single chunks left or right of it) over the zero fill with cp.async
-//    and arrive on the full barrier when those have landed.
+//    copies, on the slot's "tma" barrier; as soon as they have landed (the producer polls the
+//    "tma" and "empty" barriers in turn), the lanes copy the wrapped 16-byte chunks (whole rows
+//    above or below the grid, single chunks left or right of it) over the zero fill with
+//    cp.async and arrive on the full barrier when those have landed.
 //  mode 3, bulk rows: tiles with more wrapped chunks than the patch list holds (grids
 //    narrower than a tile): one bulk copy per contiguous segment of each row.
 //  mode 1, cp.async: no tensor map: 16-byte chunks of whole rows, wrapping or zero-filling.
