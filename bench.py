@@ -278,7 +278,9 @@ def bench_ours(args):
     xs = W["x_star_host"].pin_memory()
     xb = W["x_box_host"].pin_memory()
     yh = torch.empty((N, N, N), dtype=torch.float32).pin_memory()
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
+    # host<->device copy times vary from call to call with the host's other memory traffic:
+    # average over up to 10 steps
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
 
     def e2e_step():
         gs.stencil_apply_host(W["star"], xs, yh, 1, stream=stream)
