@@ -205,8 +205,9 @@ int stencil_batch_info(stencil_batch b, int *ntiles, int *nblocks, int *graph_ca
 
 typedef struct {
     int family;  /* kernel family chosen (STENCIL_FAMILY_*)                                     */
-    int block_x; /* threads along x                                                             */
-    int block_y; /* threads along y                                                             */
+    int block_x; /* threads along x (streaming family: 128 cells / one 16-byte vector each)      */
+    int block_y; /* threads along y (streaming family: block_x * block_y a multiple of 32, at
+                    most 224, or 256 for 3D stars of radius >= 3 with one row per thread)     */
     int vec_y;   /* rows per thread                                                             */
     int z_chunk; /* planes per CTA (3D streaming); 0 = an equal share per resident CTA          */
     int fuse;    /* time steps fused per launch                                                 */
@@ -216,7 +217,8 @@ typedef struct {
                     as the shared memory left by the CTAs that fit on an SM allows             */
 } stencil_variant;
 
-#define STENCIL_FAMILY_STREAM 1 /* one sweep per launch, z-streaming tiles, cp.async pipeline  */
+#define STENCIL_FAMILY_STREAM 1 /* one sweep per launch, z-streaming tiles on a plane ring fed
+                                   by a producer warp (tensor copies)                        */
 #define STENCIL_FAMILY_FUSED2D 2 /* several 2D sweeps per launch in a shared-memory tile      */
 
 /* stencil_plan_get_variant / stencil_plan_set_variant -- read or override the kernel variant
