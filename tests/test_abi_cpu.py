@@ -196,3 +196,81 @@ def test_library_missing_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="not built"):
         api._lib()
+
+
+def _plan_for(ndim, dims, shape, r, dtype, bc, kind):
+    if kind == "divkgrad":
+        return gs.stencil_plan(ndim, dims, "star", 1, "divkgrad", None, dtype, bc)
+    return gs.stencil_plan(ndim, dims, shape, r, "const",
+                           np.ones(len(oracle.offsets(ndim, shape, r))), dtype, bc)
+
+
+def test_autotuner_candidates_are_variants_the_library_accepts():
+    # every candidate the tuner would time is a variant the plan validation accepts, so a
+    # tuning run never spends its time on launches the library refuses (host logic only)
+    from paper_2609_06694_gb300 import autotune
+    seen = 0
+    for key in autotune.tuning_set():
+        ndim, dims, shape, r, dtype, bc, steps = key[:7]
+        kind = key[7] if len(key) > 7 else "const"
+        plan = _plan_for(ndim, dims, shape, r, dtype, bc, kind)
+        if kind == "divkgrad":
+            cands = autotune.divkgrad_candidates(dtype)
+        elif ndim == 2 and steps > 1:
+            cands = autotune.fused2d_candidates(r, steps)
+        else:
+            cands = autotune.stream_candidates(ndim, shape, r, dtype)
+        assert cands, key
+        for v in cands:
+            gs.stencil_plan_set_variant(plan, **v)
+            got = gs.stencil_plan_get_variant(plan)
+            assert all(got[k] == val for k, val in v.items()), (key, v, got)
+            seen += 1
+    assert seen > 500
+
+
+def test_streaming_thread_caps():
+    # 3D stars of radius >= 3 with one row per thread may take 8 warps of consumers, every
+    # other streaming variant 7; the CTA adds the producer warp
+    p = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "periodic")
+    gs.stencil_plan_set_variant(p, block_x=32, block_y=8, vec_y=1)
+    for by, vy in ((9, 1), (8, 2)):
+        with pytest.raises(gs.StencilError):
+            gs.stencil_plan_set_variant(p, block_x=32, block_y=by, vec_y=vy)
+    gs.stencil_plan_set_variant(p, block_x=32, block_y=7, vec_y=2)
+    b = gs.stencil_plan(3, (64, 64, 64), "box", 1, "const", np.ones(27), "bf16", "periodic")
+    gs.stencil_plan_set_variant(b, block_x=16, block_y=14, vec_y=2)
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(b, block_x=16, block_y=16, vec_y=1)
+
+
+def test_committed_dispatch_map_selects_its_entries():
+    # the dispatch map shipped with the package loads, and a plan for each of its keys picks
+    # the entry's variant (so the map still matches the library's keys and limits)
+    path = os.path.join(ROOT, "paper_2609_06694_gb300", "dispatch_map.txt")
+    gs.stencil_load_dispatch_map(path)
+    shapes = {0: "star", 1: "box", 2: "diamond"}
+    dtypes = {0: "f32", 1: "f16", 2: "bf16"}
+    kinds = {0: "const", 2: "divkgrad"}
+    names = ["family", "block_x", "block_y", "vec_y", "z_chunk", "fuse", "tile_x", "tile_y",
+             "stages"]
+    try:
+        n = 0
+        for line in open(path):
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            key, val = line.split(":")
+            ndim, shape, r, dt, bc, kind, cls = (int(t) for t in key.split())
+            want = dict(zip(names, (int(t) for t in val.split())))
+            dims = {3: (256, 256, 256), 2: (4096, 4096)}[ndim] if cls == 3 else \
+                {3: (128, 128, 128), 2: (1024, 1024)}[ndim] if cls == 2 else (512, 512)
+            assert gs.stencil_size_class(int(np.prod(dims))) == cls, (line, dims)
+            plan = _plan_for(ndim, dims, shapes[shape], r, dtypes[dt],
+                             "periodic" if bc == 1 else "dirichlet", kinds[kind])
+            got = gs.stencil_plan_get_variant(plan)
+            assert all(got[k] == v for k, v in want.items()), (line, got)
+            n += 1
+        assert n >= 10
+    finally:
+        gs.stencil_load_dispatch_map(None)
