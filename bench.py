@@ -208,7 +208,7 @@ def bench_ours(args):
     build.build()
     import paper_2609_06694_gb300 as gs
 
-    if args.only in ("divkgrad", "wave", "batch"):
+    if args.only in ("divkgrad", "var", "wave", "batch"):
         profile_case(args)
         return
     W = build_workload(device, args.grid)
@@ -344,6 +344,17 @@ def profile_case(args):
         y = torch.empty_like(u)
         for _ in range(args.warmup + args.steps):
             gs.stencil_apply_var(plan, u, [k], y, 1)
+        rc = gs.stencil_sync_status(plan)
+    elif args.only == "var":
+        # general variable coefficients: 3D star r1, 7 coefficient arrays, forward sweep
+        n = args.grid if args.grid != N else 384
+        plan = gs.stencil_plan(3, (n, n, n), "star", 1, "var", None, "f32", "dirichlet")
+        u = inputs.to_storage(inputs.uniform(3101, (n, n, n)), "f32").cuda()
+        w = [inputs.to_storage(inputs.uniform(3110 + i, (n, n, n)), "f32").cuda()
+             for i in range(7)]
+        y = torch.empty_like(u)
+        for _ in range(args.warmup + args.steps):
+            gs.stencil_apply_var(plan, u, w, y, 1)
         rc = gs.stencil_sync_status(plan)
     elif args.only == "wave":
         n3 = (256, 256, 256)
@@ -612,7 +623,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", choices=["star", "box", "divkgrad", "wave", "batch"], default=None,
+    ap.add_argument("--only", choices=["star", "box", "divkgrad", "var", "wave", "batch"],
+                    default=None,
                     help="profiling case: only the 1-sweep call of one stencil, no JSON line")
     ap.add_argument("--grid", type=int, default=N, help="cube side (profiling cases only)")
     ap.add_argument("--suite", action="store_true",
