@@ -101,9 +101,9 @@ def divkgrad_candidates(dtype, quick=False):
     bx = 128 // (16 // (4 if dtype == "f32" else 2))
     heights = (1, 2, 3, 4, 6, 7, 8, 12, 14) if not quick else (4, 7, 14)
     out = []
-    for by, zc in itertools.product(heights, (0, 16, 32, 64, 128)):
+    for by, vy, zc in itertools.product(heights, (1, 2), (0, 16, 32, 64, 128)):
         if bx * by <= 224 and (bx * by) % 32 == 0:
-            out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=1,
+            out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=vy,
                             z_chunk=zc, fuse=1, tile_x=0, tile_y=0, stages=0))
     return out
 

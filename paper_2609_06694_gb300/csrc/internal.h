@@ -80,6 +80,7 @@ struct VarLaunch {
     const void *const *arrays;  // VAR: npts arrays; DIVKGRAD: k
     int narrays;
     int block_y, z_chunk;
+    int vec_y = 1;  // div(k grad u): output rows per thread (1 or 2)
     cudaStream_t stream;
 };
 #define GST_DECLARE_VAR(DT)                               \

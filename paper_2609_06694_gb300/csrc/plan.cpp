@@ -123,10 +123,12 @@ static bool lookup_map(const stencil_plan_s &p, stencil_variant *out) {
 
 int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
     if (p.kind != STENCIL_CONST) {
-        // variable-coefficient kernels: 128-cell tiles, block_y rows of one output row per
-        // thread (at most 224 threads), z chunks of z_chunk planes (0: whole columns for the
-        // general sweeps, an equal share per resident CTA for div(k grad u))
-        if (v.family != STENCIL_FAMILY_STREAM || v.vec_y != 1 || v.fuse != 1 ||
+        // variable-coefficient kernels: 128-cell tiles, block_y rows of threads with one output
+        // row each (div(k grad u): one or two), at most 224 threads, z chunks of z_chunk planes
+        // (0: whole columns for the general sweeps, an equal share per resident CTA for
+        // div(k grad u))
+        const bool vy_ok = v.vec_y == 1 || (v.vec_y == 2 && p.kind == STENCIL_DIVKGRAD);
+        if (v.family != STENCIL_FAMILY_STREAM || !vy_ok || v.fuse != 1 ||
             v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
             v.block_x * v.block_y > 224 || (v.block_x * v.block_y) % 32 != 0 || v.z_chunk < 0)
             return STENCIL_ERR_BADARG;
@@ -607,6 +609,7 @@ static int run_var_steps(stencil_plan_s &p, const void *in, const void *const *a
     L.narrays = p.kind == STENCIL_DIVKGRAD ? 1 : (int)p.npts;
     L.block_y = p.variant.block_y;
     L.z_chunk = p.variant.z_chunk;
+    L.vec_y = p.variant.vec_y;
     L.stream = s;
     const void *src = in;
     for (int g = 0; g < steps; ++g) {

@@ -319,32 +319,34 @@ template <typename T> struct DivkParams {
     int *err;
 };
 
-template <typename T, int NDIM> struct DivkKernel {
+// VY: output rows per consumer thread (1 or 2); two rows share one plane's wait, release and
+// slot addressing, and the y face between them reads rows the thread loads anyway.
+template <typename T, int NDIM, int VY = 1> struct DivkKernel {
     static constexpr int VX = 16 / (int)sizeof(T), A = VX, TX = 128, BX = TX / VX, R = 1;
     static constexpr int PITCH = TX + 2 * A;
     static constexpr int RZ = NDIM == 3 ? 1 : 0;
     static constexpr int MAX_THREADS = 224;  // consumers; the CTA adds the producer warp
     __host__ __device__ static constexpr uint32_t field_bytes(int by) {
-        return RingLayout::field_size(PITCH, by + 2 * R, (int)sizeof(T));
+        return RingLayout::field_size(PITCH, by * VY + 2 * R, (int)sizeof(T));
     }
     static size_t smem_bytes(int by, int nstage) {
         return RingLayout::bytes(2 * field_bytes(by), nstage);
     }
 };
 
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(DivkKernel<T, NDIM>::MAX_THREADS + 32)
+template <typename T, int NDIM, int VY>
+__global__ void __launch_bounds__(DivkKernel<T, NDIM, VY>::MAX_THREADS + 32)
     divkgrad_kernel(const __grid_constant__ DivkParams<T> p) {
-    using K = DivkKernel<T, NDIM>;
+    using K = DivkKernel<T, NDIM, VY>;
     constexpr int VX = K::VX, A = K::A, TX = K::TX, BX = K::BX, R = 1, PITCH = K::PITCH;
     constexpr int RZ = K::RZ;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    // blockDim = (BX, by + 32 / BX): by rows of consumer threads (one output row each), then
+    // blockDim = (BX, by + 32 / BX): by rows of consumer threads (VY output rows each), then
     // the producer warp
     const int by = (int)blockDim.y - 32 / BX;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * BX + tx, ncons = BX * by, lane = tid & 31;
-    const int TY = by, rows = TY + 2 * R;
+    const int TY = by * VY, rows = TY + 2 * R;
     Ring g;
     g.setup(smem_raw, K::field_bytes(by), 2, p.nstage);
     if (tid == 0) g.init(ncons / 32);
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(DivkKernel<T, NDIM>::MAX_THREADS + 32)
     }
 
     const size_t pstride = (size_t)nx * ny;
-    const int off = (ty + R) * PITCH + A + tx * VX;  // the thread's first cell in a field
+    const int off = (ty * VY + R) * PITCH + A + tx * VX;  // the thread's first cell in a field
     const uint32_t kofs = g.field_bytes / sizeof(T);  // k field, in elements after u
     RingPos wpos, rpos;  // next plane to wait for / to release
     bool failed = false;
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(DivkKernel<T, NDIM>::MAX_THREADS + 32)
     for (long long w = wk.w_first; w < wk.w_end && !failed;) {
         const RingPiece q = wk.piece_at(w);
         w += q.z_end - q.z_begin;
-        const int ox = q.x0 + tx * VX, oy = q.y0 + ty;
+        const int ox = q.x0 + tx * VX, oy0 = q.y0 + ty * VY;
         const bool vec = aligned && ox + VX <= nx;
         const int nvalid = nx - ox;
         // prologue: planes z_begin - RZ .. z_begin + RZ - 1
@@ -401,80 +403,92 @@ __global__ void __launch_bounds__(DivkKernel<T, NDIM>::MAX_THREADS + 32)
             int s0 = wpos.slot - 1 - RZ;
             if (s0 < 0) s0 += g.ns;
             const T *su = reinterpret_cast<const T *>(g.slot_ptr(s0));
-            const bool active = oy < ny && ox < nx;
-            float acc[VX];
+            float acc2[VY][VX];
 #pragma unroll
-            for (int i = 0; i < VX; ++i) acc[i] = 0.0f;
-            if (active) {
-                const int i0 = off;
-                float u0[VX + 2], k0[VX + 2];  // centre row with one cell each side
-                load_span<T, -1, VX + 1, -1>(su + i0, u0);
-                load_span<T, -1, VX + 1, -1>(su + kofs + i0, k0);
-                // Each face adds (k_c + k_n) (u_n - u_c); the sum is halved at the end (exact,
-                // so this equals the half-face form bit for bit).  A neighbour outside a
-                // Dirichlet grid has u = 0 and k = k_c.  ALLIN: no neighbour of this thread's
-                // cells is outside the grid, so no face needs a select.
-                auto compute = [&](auto allin_c) {
-                    constexpr bool ALLIN = decltype(allin_c)::value;
-                    auto face = [&](int i, float un, float kn, bool inside) {
-                        const float kc = k0[i + 1];
-                        const bool in = ALLIN || inside;
-                        const float ssum = kc + (in ? kn : kc);
-                        const float d = (in ? un : 0.0f) - u0[i + 1];
-                        acc[i] = fmaf(ssum, d, acc[i]);
+            for (int v = 0; v < VY; ++v)
+#pragma unroll
+                for (int i = 0; i < VX; ++i) acc2[v][i] = 0.0f;
+#pragma unroll
+            for (int v = 0; v < VY; ++v) {
+                const int oy = oy0 + v;
+                float(&acc)[VX] = acc2[v];
+                const bool active = oy < ny && ox < nx;
+                if (active) {
+                    const int i0 = off + v * PITCH;
+                    float u0[VX + 2], k0[VX + 2];  // centre row with one cell each side
+                    load_span<T, -1, VX + 1, -1>(su + i0, u0);
+                    load_span<T, -1, VX + 1, -1>(su + kofs + i0, k0);
+                    // Each face adds (k_c + k_n) (u_n - u_c); the sum is halved at the end (exact,
+                    // so this equals the half-face form bit for bit).  A neighbour outside a
+                    // Dirichlet grid has u = 0 and k = k_c.  ALLIN: no neighbour of this thread's
+                    // cells is outside the grid, so no face needs a select.
+                    auto compute = [&](auto allin_c) {
+                        constexpr bool ALLIN = decltype(allin_c)::value;
+                        auto face = [&](int i, float un, float kn, bool inside) {
+                            const float kc = k0[i + 1];
+                            const bool in = ALLIN || inside;
+                            const float ssum = kc + (in ? kn : kc);
+                            const float d = (in ? un : 0.0f) - u0[i + 1];
+                            acc[i] = fmaf(ssum, d, acc[i]);
+                        };
+                        // axes in the oracle's order: z, y, x; within an axis the + face, then -
+                        if constexpr (NDIM == 3) {
+                            const int sp = s0 + 1 == g.ns ? 0 : s0 + 1;
+                            const int sm = s0 == 0 ? g.ns - 1 : s0 - 1;
+                            const T *up_ = reinterpret_cast<const T *>(g.slot_ptr(sp)) + i0;
+                            const T *um_ = reinterpret_cast<const T *>(g.slot_ptr(sm)) + i0;
+                            float up[VX], kp[VX], um[VX], km[VX];
+                            load_span<T, 0, VX, 0>(up_, up);
+                            load_span<T, 0, VX, 0>(up_ + kofs, kp);
+                            load_span<T, 0, VX, 0>(um_, um);
+                            load_span<T, 0, VX, 0>(um_ + kofs, km);
+                            const bool inp = periodic || zo + 1 < nz, inm = periodic || zo - 1 >= 0;
+#pragma unroll
+                            for (int i = 0; i < VX; ++i) {
+                                face(i, up[i], kp[i], inp);
+                                face(i, um[i], km[i], inm);
+                            }
+                        }
+                        {
+                            float up[VX], kp[VX], um[VX], km[VX];
+                            load_span<T, 0, VX, 0>(su + i0 + PITCH, up);
+                            load_span<T, 0, VX, 0>(su + kofs + i0 + PITCH, kp);
+                            load_span<T, 0, VX, 0>(su + i0 - PITCH, um);
+                            load_span<T, 0, VX, 0>(su + kofs + i0 - PITCH, km);
+                            const bool inp = periodic || oy + 1 < ny, inm = periodic || oy - 1 >= 0;
+#pragma unroll
+                            for (int i = 0; i < VX; ++i) {
+                                face(i, up[i], kp[i], inp);
+                                face(i, um[i], km[i], inm);
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < VX; ++i) {
+                            const bool inp = periodic || ox + i + 1 < nx;
+                            const bool inm = periodic || ox + i - 1 >= 0;
+                            face(i, u0[i + 2], k0[i + 2], inp);
+                            face(i, u0[i], k0[i], inm);
+                        }
                     };
-                    // axes in the oracle's order: z, y, x; within an axis the + face, then -
-                    if constexpr (NDIM == 3) {
-                        const int sp = s0 + 1 == g.ns ? 0 : s0 + 1;
-                        const int sm = s0 == 0 ? g.ns - 1 : s0 - 1;
-                        const T *up_ = reinterpret_cast<const T *>(g.slot_ptr(sp)) + i0;
-                        const T *um_ = reinterpret_cast<const T *>(g.slot_ptr(sm)) + i0;
-                        float up[VX], kp[VX], um[VX], km[VX];
-                        load_span<T, 0, VX, 0>(up_, up);
-                        load_span<T, 0, VX, 0>(up_ + kofs, kp);
-                        load_span<T, 0, VX, 0>(um_, um);
-                        load_span<T, 0, VX, 0>(um_ + kofs, km);
-                        const bool inp = periodic || zo + 1 < nz, inm = periodic || zo - 1 >= 0;
-#pragma unroll
-                        for (int i = 0; i < VX; ++i) {
-                            face(i, up[i], kp[i], inp);
-                            face(i, um[i], km[i], inm);
-                        }
-                    }
-                    {
-                        float up[VX], kp[VX], um[VX], km[VX];
-                        load_span<T, 0, VX, 0>(su + i0 + PITCH, up);
-                        load_span<T, 0, VX, 0>(su + kofs + i0 + PITCH, kp);
-                        load_span<T, 0, VX, 0>(su + i0 - PITCH, um);
-                        load_span<T, 0, VX, 0>(su + kofs + i0 - PITCH, km);
-                        const bool inp = periodic || oy + 1 < ny, inm = periodic || oy - 1 >= 0;
-#pragma unroll
-                        for (int i = 0; i < VX; ++i) {
-                            face(i, up[i], kp[i], inp);
-                            face(i, um[i], km[i], inm);
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < VX; ++i) {
-                        const bool inp = periodic || ox + i + 1 < nx;
-                        const bool inm = periodic || ox + i - 1 >= 0;
-                        face(i, u0[i + 2], k0[i + 2], inp);
-                        face(i, u0[i], k0[i], inm);
-                    }
-                };
-                const bool all_in = periodic || (ox > 0 && ox + VX < nx && oy > 0 && oy + 1 < ny &&
-                                                 (NDIM == 2 || (zo > 0 && zo + 1 < nz)));
-                if (all_in)
-                    compute(std::true_type{});
-                else
-                    compute(std::false_type{});
-            }
+                    const bool all_in =
+                        periodic || (ox > 0 && ox + VX < nx && oy > 0 && oy + 1 < ny &&
+                                     (NDIM == 2 || (zo > 0 && zo + 1 < nz)));
+                    if (all_in)
+                        compute(std::true_type{});
+                    else
+                        compute(std::false_type{});
+                }
+            }  // rows of the thread
             release_plane();  // plane zo - RZ has been read for the last time (whole warp)
-            if (active) {
 #pragma unroll
-                for (int i = 0; i < VX; ++i) acc[i] *= 0.5f;
-                store_cells<T, VX>(p.out + (size_t)zo * pstride + (size_t)oy * nx + ox, vec,
-                                   nvalid, acc);
+            for (int v = 0; v < VY; ++v) {
+                const int oy = oy0 + v;
+                if (oy < ny && ox < nx) {
+#pragma unroll
+                    for (int i = 0; i < VX; ++i) acc2[v][i] *= 0.5f;
+                    store_cells<T, VX>(p.out + (size_t)zo * pstride + (size_t)oy * nx + ox, vec,
+                                       nvalid, acc2[v]);
+                }
             }
         }
         // the last 2RZ planes of the piece were only read as neighbours

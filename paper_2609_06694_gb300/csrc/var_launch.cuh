@@ -83,9 +83,9 @@ template <typename T, bool ADJ> int launch_var_dt(const VarLaunch &L) {
     return -1;
 }
 
-template <typename T, int NDIM> int launch_divkgrad_nd(const VarLaunch &L) {
-    using K = DivkKernel<T, NDIM>;
-    auto kern = divkgrad_kernel<T, NDIM>;
+template <typename T, int NDIM, int VY> int launch_divkgrad_nd(const VarLaunch &L) {
+    using K = DivkKernel<T, NDIM, VY>;
+    auto kern = divkgrad_kernel<T, NDIM, VY>;
     int by = L.block_y > 0 ? L.block_y : 128 / K::BX;
     by = std::min(by, K::MAX_THREADS / K::BX);
     if ((K::BX * by) % 32) return -1;
@@ -103,9 +103,9 @@ template <typename T, int NDIM> int launch_divkgrad_nd(const VarLaunch &L) {
                         (uintptr_t)L.out % 16 == 0;
     p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
     p.tiles_x = (int)((nx + K::TX - 1) / K::TX);
-    p.tiles_y = (int)((ny + by - 1) / by);
+    p.tiles_y = (int)((ny + by * VY - 1) / (by * VY));
     p.err = nullptr;
-    const int rows = by + 2;
+    const int rows = by * VY + 2;
     p.use_tma = (p.aligned &&
                  encode_plane_map<T>(&p.tmap[0], L.in, nx, ny, nz, K::PITCH, rows) &&
                  encode_plane_map<T>(&p.tmap[1], L.arrays[0], nx, ny, nz, K::PITCH, rows))
@@ -145,7 +145,10 @@ template <typename T, int NDIM> int launch_divkgrad_nd(const VarLaunch &L) {
 }
 
 template <typename T> int launch_divkgrad_t(const VarLaunch &L) {
-    return L.ndim == 3 ? launch_divkgrad_nd<T, 3>(L) : launch_divkgrad_nd<T, 2>(L);
+    if (L.vec_y == 2)
+        return L.ndim == 3 ? launch_divkgrad_nd<T, 3, 2>(L) : launch_divkgrad_nd<T, 2, 2>(L);
+    if (L.vec_y != 1) return -1;
+    return L.ndim == 3 ? launch_divkgrad_nd<T, 3, 1>(L) : launch_divkgrad_nd<T, 2, 1>(L);
 }
 
 }  // namespace gst

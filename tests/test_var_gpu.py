@@ -84,8 +84,8 @@ def test_var_rejects_missing_arrays_and_unsupported_sets():
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
 def test_divkgrad_work_splits(dtype, bc):
     # one equal share of the (tile, z) planes per resident CTA (z_chunk 0: a CTA's planes span
-    # several tiles), short chunks that end mid-column, and several tile heights: every split
-    # gives the same bits and matches the oracle
+    # several tiles), short chunks that end mid-column, several tile heights, one and two rows
+    # per thread: every split gives the same bits and matches the oracle
     dims = (23, 45, 264)
     plan = gs.stencil_plan(3, dims, "star", 1, "divkgrad", None, dtype, bc)
     k = inputs.to_storage(inputs.lognormal_k(3012, dims), dtype)
@@ -94,15 +94,18 @@ def test_divkgrad_work_splits(dtype, bc):
     base = gs.stencil_plan_get_variant(plan)
     bx = base["block_x"]
     first = None
-    for by, zc in ((4, 0), (2 if bx == 32 else 4, 0), (7 if bx == 32 else 14, 5), (1 if bx == 32 else 2, 9)):
-        gs.stencil_plan_set_variant(plan, **dict(base, block_y=by, z_chunk=zc, stages=0))
+    f = 1 if bx == 32 else 2  # 16-bit rows of 128 cells take 16 threads: twice the rows
+    for by, vy, zc in ((4, 1, 0), (2 * f, 1, 0), (7 * f, 1, 5), (f, 1, 9), (4 * f, 2, 16),
+                       (7 * f, 2, 0), (f, 2, 3)):
+        gs.stencil_plan_set_variant(plan, **dict(base, block_y=by, vec_y=vy, z_chunk=zc,
+                                                 stages=0))
         y = torch.empty_like(u, device="cuda")
         gs.stencil_apply_var(plan, u.cuda(), [k.cuda()], y, 1)
         assert gs.stencil_sync_status(plan) == 0
-        assert relerr(inputs.stored_values(y), ref) < TOL[dtype], (by, zc)
+        assert relerr(inputs.stored_values(y), ref) < TOL[dtype], (by, vy, zc)
         if first is None:
             first = y.clone()
-        assert torch.equal(y, first), (by, zc)
+        assert torch.equal(y, first), (by, vy, zc)
 
 
 @pytest.mark.parametrize("ndim", [2, 3])
