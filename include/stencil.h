@@ -208,8 +208,10 @@ typedef struct {
     int block_x; /* threads along x (streaming family: 128 cells / one 16-byte vector each)      */
     int block_y; /* threads along y (streaming family: block_x * block_y a multiple of 32, at
                     most 224, or 256 for 3D stars of radius >= 3 with one row per thread)     */
-    int vec_y;   /* rows per thread                                                             */
-    int z_chunk; /* planes per CTA (3D streaming); 0 = an equal share per resident CTA          */
+    int vec_y;   /* rows per thread (streaming 1, 2 or 4 by stencil; div(k grad u) 1 or 2;
+                    general variable-coefficient sweeps 1)                                   */
+    int z_chunk; /* planes per CTA (3D); 0 = an equal share per resident CTA (streaming and
+                    div(k grad u)) or whole columns (general variable-coefficient sweeps)     */
     int fuse;    /* time steps fused per launch                                                 */
     int tile_x;  /* output tile width of fused 2D kernels (0 = default)                         */
     int tile_y;  /* output tile height of fused 2D kernels (0 = default)                        */
