@@ -1,8 +1,9 @@
 """FP64 stencil oracle (TEST INFRASTRUCTURE ONLY).
 
-Python access to the plain single-threaded C oracle in ``stencil_oracle.c``.  Only the test
-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline / reference leg may import
-this package.  It shares no code with the CUDA library and never imports it.
+Python access to the plain C oracle in ``stencil_oracle.c`` (single-threaded by default;
+``use_threads`` switches to the same source built with OpenMP, which gives the same bits).
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline / reference
+leg may import this package.  It shares no code with the CUDA library and never imports it.
 
 Functions take and return float64 numpy arrays in row-major layout (last axis fastest); grid
 dimensions are given slowest axis first.  Paper references: Sec. 2.1 (stencil update, offset
@@ -21,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "stencil_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_LIB_MT = os.path.join(_LIB_DIR, "liboracle_mt.so")  # the same source with OpenMP
 
 STAR, BOX, DIAMOND = 0, 1, 2
 SHAPES = {"star": STAR, "box": BOX, "diamond": DIAMOND}
@@ -30,24 +32,48 @@ ROUND = {"none": 0, "f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fused multiply-add, so every host gives the same bits)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+    """Compile the oracle with gcc (no fused multiply-add, so every host gives the same bits):
+    a single-threaded library and the same source with OpenMP (cell loops over host threads,
+    identical results)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
-    tmp = _LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-                           _SRC, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB)
+    for lib, extra in ((_LIB, []), (_LIB_MT, ["-fopenmp"])):
+        if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(_SRC):
+            continue
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC",
+                               "-shared"] + extra + [_SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, lib)
     return _LIB
 
 
-_lib = None
+_libs = {}
+_threads = 1
+
+
+def use_threads(n: int = 0) -> int:
+    """Run the oracle's cell loops on n host threads from now on (0: every core, 1: the
+    single-threaded build).  Results are bit-for-bit the same; returns the thread count."""
+    global _threads
+    if n == 1:
+        _threads = 1
+        return 1
+    _threads = int(_open(_LIB_MT).orc_set_threads(int(n)))
+    return _threads
+
+
+def threads() -> int:
+    """Host threads the oracle currently uses."""
+    return _threads
 
 
 def _L():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+    return _open(_LIB if _threads == 1 else _LIB_MT)
+
+
+def _open(path):
+    if path not in _libs:
+        build()
+        lib = ctypes.CDLL(path)
         P = ctypes.c_void_p
         I64 = ctypes.c_int64
         I = ctypes.c_int
@@ -72,8 +98,10 @@ def _L():
         lib.orc_misfit.restype = D
         lib.orc_wave_gradient.argtypes = [P, I64, P, P, P, D, D, I, I64, P, I64, P, I, P, P]
         lib.orc_wave_gradient.restype = I
-        _lib = lib
-    return _lib
+        lib.orc_set_threads.argtypes = [I]
+        lib.orc_set_threads.restype = I
+        _libs[path] = lib
+    return _libs[path]
 
 
 def _f64(a):

@@ -1,10 +1,11 @@
 /*
  * FP64 stencil oracle -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded double-precision statement of what the stencil library
- * computes.  Only the test suite, the package's smoke check and the benchmark's CPU-baseline
- * leg load it; the library never does, and this file shares no header, table or helper with
- * the CUDA path.  Every loop visits cells in row-major order (last axis fastest) and sums the
+ * A plain, slow double-precision statement of what the stencil library computes (one thread,
+ * or its cell loops split over host threads when built with OpenMP; the bits are the same).
+ * Only the test suite, the package's smoke check and the benchmark's CPU-baseline leg load
+ * it; the library never does, and this file shares no header, table or helper with the CUDA
+ * path.  Every loop visits cells in row-major order (last axis fastest) and sums the
  * offsets of a stencil in canonical order, one term at a time, starting from 0.0.  Build with
  * -ffp-contract=off so that no multiply-add is fused and the results are identical on every
  * host.
@@ -34,6 +35,31 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Built twice from this file: without OpenMP (one thread), and with -fopenmp, where the cell
+ * loops below are split over threads.  Every cell is written by one thread and its terms are
+ * summed in the same order either way, so both builds give the same bits. */
+#ifdef _OPENMP
+#include <omp.h>
+#define PARALLEL_CELLS _Pragma("omp parallel for schedule(static)")
+#else
+#define PARALLEL_CELLS
+#endif
+
+/* Threads the cell loops use from now on (n <= 0: every host core); returns the count in
+ * effect, 1 for the build without OpenMP. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n <= 0)
+        n = omp_get_num_procs();
+    omp_set_num_threads(n);
+    return n;
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 #define ORC_STAR 0
 #define ORC_BOX 1
@@ -145,8 +171,9 @@ void orc_sweep_const(int ndim, const int64_t *dims, int64_t npts, const int32_t 
                      const double *c, int bc, const double *in, double *out)
 {
     int64_t ncell = cell_count(ndim, dims);
-    int64_t p[3];
+    PARALLEL_CELLS
     for (int64_t lin = 0; lin < ncell; ++lin) {
+        int64_t p[3];
         unravel(ndim, dims, lin, p);
         double acc = 0.0;
         for (int64_t o = 0; o < npts; ++o) {
@@ -164,8 +191,9 @@ void orc_sweep_const_points(int ndim, const int64_t *dims, int64_t npts, const i
                             const double *c, int bc, const double *in, int64_t nsel,
                             const int64_t *sel, double *out)
 {
-    int64_t p[3];
+    PARALLEL_CELLS
     for (int64_t s = 0; s < nsel; ++s) {
+        int64_t p[3];
         unravel(ndim, dims, sel[s], p);
         double acc = 0.0;
         for (int64_t o = 0; o < npts; ++o) {
@@ -185,8 +213,9 @@ void orc_sweep_var(int ndim, const int64_t *dims, int64_t npts, const int32_t *o
                    const double *w, int bc, const double *in, double *out)
 {
     int64_t ncell = cell_count(ndim, dims);
-    int64_t p[3];
+    PARALLEL_CELLS
     for (int64_t lin = 0; lin < ncell; ++lin) {
+        int64_t p[3];
         unravel(ndim, dims, lin, p);
         double acc = 0.0;
         for (int64_t o = 0; o < npts; ++o) {
@@ -207,8 +236,9 @@ void orc_sweep_const_adjoint(int ndim, const int64_t *dims, int64_t npts, const 
                              const double *c, int bc, const double *y, double *out)
 {
     int64_t ncell = cell_count(ndim, dims);
-    int64_t q[3];
+    PARALLEL_CELLS
     for (int64_t lin = 0; lin < ncell; ++lin) {
+        int64_t q[3];
         unravel(ndim, dims, lin, q);
         double acc = 0.0;
         for (int64_t o = 0; o < npts; ++o) {
@@ -224,8 +254,9 @@ void orc_sweep_var_adjoint(int ndim, const int64_t *dims, int64_t npts, const in
                            const double *w, int bc, const double *y, double *out)
 {
     int64_t ncell = cell_count(ndim, dims);
-    int64_t q[3];
+    PARALLEL_CELLS
     for (int64_t lin = 0; lin < ncell; ++lin) {
+        int64_t q[3];
         unravel(ndim, dims, lin, q);
         double acc = 0.0;
         for (int64_t o = 0; o < npts; ++o) {
@@ -272,8 +303,9 @@ void orc_divkgrad(int ndim, const int64_t *dims, const double *k, int bc, const 
                   double *out)
 {
     int64_t ncell = cell_count(ndim, dims);
-    int64_t p[3];
+    PARALLEL_CELLS
     for (int64_t lin = 0; lin < ncell; ++lin) {
+        int64_t p[3];
         unravel(ndim, dims, lin, p);
         double acc = 0.0;
         for (int axis = 0; axis < ndim; ++axis) {
@@ -293,8 +325,9 @@ void orc_divkgrad_weights(int ndim, const int64_t *dims, const double *k, int bc
     int64_t ncell = cell_count(ndim, dims);
     int32_t offs[7 * 3];
     int64_t npts = orc_offsets(ndim, ORC_STAR, 1, offs);
-    int64_t p[3];
+    PARALLEL_CELLS
     for (int64_t lin = 0; lin < ncell; ++lin) {
+        int64_t p[3];
         unravel(ndim, dims, lin, p);
         double centre = 0.0;
         for (int64_t o = 0; o < npts; ++o)
@@ -392,6 +425,7 @@ void orc_round(int64_t n, double *x, int mode)
 {
     if (mode == ORC_ROUND_NONE)
         return;
+    PARALLEL_CELLS
     for (int64_t i = 0; i < n; ++i)
         x[i] = orc_round_scalar(x[i], mode);
 }

@@ -122,6 +122,60 @@ def test_dirichlet_sweep_is_zero_padded_convolution(ndim, shape, r):
     assert relerr(oracle.sweep_const_adjoint(x, offs, c, "dirichlet"), crop_t) < 1e-12
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("r", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_point_evaluation_is_the_sweep_at_every_cell(ndim, shape, r, bc):
+    """The point evaluator (the reference of the full-size spot checks) against the FFT
+    convolution at every cell of small grids -- corners, edges, faces and, for periodic grids
+    smaller than the stencil, cells whose reads wrap several times -- in a shuffled order with
+    repeats, and bit for bit against the whole-grid sweep."""
+    offs = oracle.offsets(ndim, shape, r)
+    for g, dims in enumerate(GRIDS[ndim]):
+        c = inputs.uniform(950 + 10 * r + g, (len(offs),))
+        x = inputs.uniform(960 + 10 * r + g, dims)
+        if bc == "periodic":
+            want = fft_periodic_sweep(x, offs, c)
+        else:
+            pad = np.pad(x, r)
+            want = fft_periodic_sweep(pad, offs, c)[tuple(slice(r, r + n) for n in dims)]
+        n = int(np.prod(dims))
+        sel = np.random.default_rng(g).permutation(np.concatenate([np.arange(n), [0, n - 1]]))
+        got = oracle.sweep_const_points(x, offs, c, bc, sel)
+        assert relerr(got, want.ravel()[sel]) < 1e-12
+        assert np.array_equal(got, oracle.sweep_const(x, offs, c, bc).ravel()[sel])
+
+
+def test_threaded_build_gives_the_same_bits():
+    """The OpenMP build of the oracle splits cell loops over threads only: every function used
+    by the parity tests returns identical bits to the single-threaded build."""
+    dims = (9, 14, 33)
+    offs = oracle.offsets(3, "box", 2)
+    c = inputs.uniform(970, (len(offs),))
+    x = inputs.uniform(971, dims)
+    k = 1.0 + inputs.uniform(972, dims) ** 2
+    sel = np.arange(0, x.size, 7)
+
+    def everything():
+        return [oracle.sweep_const(x, offs, c, "periodic"),
+                oracle.sweep_const_adjoint(x, offs, c, "dirichlet"),
+                oracle.sweep_const_points(x, offs, c, "periodic", sel),
+                oracle.divkgrad(x, k, "dirichlet"),
+                oracle.run(x, "const", "dirichlet", 3, offs=offs, coeffs=c, round_fmt="bf16"),
+                oracle.run(x, "divkgrad", "periodic", 2, coeffs=k, round_fmt="f16")]
+
+    assert oracle.threads() == 1
+    one = everything()
+    try:
+        assert oracle.use_threads(4) >= 1
+        many = everything()
+    finally:
+        oracle.use_threads(1)
+    for a, b in zip(one, many):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("shape", SHAPES)
 def test_single_impulse_gives_flipped_weights_clipped(shape):
     offs = oracle.offsets(3, shape, 2)
