@@ -25,8 +25,9 @@
  *    the GPU, slower).
  *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Launches
  *    are asynchronous; argument errors are returned at once, CUDA launch errors as
- *    STENCIL_ERR_CUDA, and errors detected by a kernel (a bounded wait that expired, an index
- *    check) are latched in a device word read by stencil_sync_status / stencil_batch_status.
+ *    STENCIL_ERR_CUDA, and errors detected by a kernel (a bounded wait that expired) are
+ *    latched in the plan's device status word, read by stencil_sync_status (batches:
+ *    stencil_batch_status; wave plans: wave_sync_status).
  *  - A plan is not thread-safe: do not use one handle from two host threads at once.
  */
 #ifndef GB300_STENCIL_H
@@ -51,6 +52,7 @@ extern "C" {
 #define STENCIL_STAR 0
 #define STENCIL_BOX 1
 #define STENCIL_DIAMOND 2
+#define STENCIL_CUSTOM 3   /* any offset set of max-norm <= radius, given by the caller       */
 
 #define STENCIL_F32 0
 #define STENCIL_F16 1
@@ -75,19 +77,36 @@ typedef struct stencil_batch_s *stencil_batch;
  *            stencil_destroy).  The call allocates no device memory.
  *   ndim     2 or 3; dims[ndim] extents, slowest first, each >= 1.
  *   shape    STENCIL_STAR / BOX / DIAMOND; radius 1..4 (kind DIVKGRAD: star, radius 1).
- *   kind     STENCIL_CONST: coeffs[ncoeffs] holds one weight per offset in canonical order
- *            (ncoeffs must equal the offset count); the values are copied.
+ *            STENCIL_CUSTOM: the offset set S is any set of ncoeffs distinct offsets (Sec. 2.1
+ *            defines the sweep over an arbitrary S) listed in custom_offsets[ncoeffs * ndim]
+ *            (int32, slowest component first, host memory, copied), every component within
+ *            [-radius, radius]; kind must be STENCIL_CONST (else UNSUPPORTED).  The sweep runs
+ *            on the kernel of the smallest compiled star, diamond or box set containing S,
+ *            with weight 0 on its other offsets (so the result is the sum over S alone;
+ *            terms are added in that set's canonical order).
+ *   kind     STENCIL_CONST: coeffs[ncoeffs] holds one weight per offset -- in canonical order,
+ *            or in the order of custom_offsets (ncoeffs must equal the offset count); the
+ *            values are copied.
  *            STENCIL_VAR / STENCIL_DIVKGRAD: coeffs must be NULL and ncoeffs 0; the arrays are
  *            passed to stencil_apply_var.
+ *   custom_offsets  NULL unless shape is STENCIL_CUSTOM.
  *   dtype    storage type of every grid array (STENCIL_F32 / F16 / BF16).
  *   boundary STENCIL_DIRICHLET0 or STENCIL_PERIODIC.
- * Errors: BADARG for out-of-range values or a count mismatch; UNSUPPORTED for a combination
- * without a kernel.  The kernel choice comes from the dispatch map (stencil_load_dispatch_map)
- * or from built-in defaults. */
+ * Errors: BADARG for out-of-range values, a count mismatch, repeated custom offsets or
+ * custom_offsets given for another shape (or missing for STENCIL_CUSTOM); UNSUPPORTED for a
+ * combination without a kernel; OOM when 65536 plans are alive.  The kernel choice comes from
+ * the dispatch map (stencil_load_dispatch_map) or from built-in defaults. */
 int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, int radius,
-                 int kind, const double *coeffs, int64_t ncoeffs, int dtype, int boundary);
+                 int kind, const double *coeffs, int64_t ncoeffs, const int32_t *custom_offsets,
+                 int dtype, int boundary);
 
-/* stencil_offsets -- the plan's offsets in canonical order.  Writes min(n, capacity) rows of
+/* stencil_plan_kernel_set -- the compiled offset set the plan's kernels run: its shape
+ * (STENCIL_STAR / BOX / DIAMOND) and radius; for a custom plan, the set chosen to contain it.
+ * Either pointer may be NULL. */
+int stencil_plan_kernel_set(stencil_handle h, int *shape, int *radius);
+
+/* stencil_offsets -- the plan's offsets in canonical order (a custom plan: in the order the
+ * caller gave them, the order of its coefficients).  Writes min(n, capacity) rows of
  * ndim int32 (slowest component first) to offsets_out (may be NULL when capacity is 0) and the
  * full count to *n. */
 int stencil_offsets(stencil_handle h, int32_t *offsets_out, int64_t capacity, int64_t *n);
@@ -144,10 +163,10 @@ int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, in
 /* stencil_apply_noalloc -- stencil_apply for callers that may not allocate device memory.
  * The paper has no counterpart; this is a library service.  stencil_apply obtains its
  * multi-step scratch grid with cudaMalloc on first use, which some callers cannot allow: code
- * inside a framework whose memory pool already holds the device's memory, latency-critical
- * loops that cannot absorb cudaMalloc's implicit device synchronisation, and work issued while
- * a stream is being captured.  This call computes the same sweeps (same kernels, same step
- * grouping, same results) but ping-pongs through a fixed array compiled into the library:
+ * inside a framework whose memory pool already holds the device's memory, and
+ * latency-critical loops that cannot absorb cudaMalloc's implicit device synchronisation.
+ * This call computes the same sweeps (same kernels, same step grouping, same results) but
+ * ping-pongs through a fixed array compiled into the library:
  *   - no cudaMalloc/cudaFree or other allocating call is made;
  *   - grids larger than STENCIL_NOALLOC_SCRATCH_BYTES (in bytes of the storage type) are
  *     rejected with STENCIL_ERR_BADARG before anything is launched;
@@ -161,8 +180,22 @@ int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, in
 int stencil_apply_noalloc(stencil_handle h, const void *in, void *out, int steps, void *stream);
 
 /* stencil_sync_status -- synchronise `stream` and return the first error latched by a kernel
- * of this plan since the last call (then clear it). */
+ * of this plan since the last call (then clear it): STENCIL_ERR_TIMEOUT when a bounded
+ * device-side wait of the plane ring (the streaming and div(k grad u) kernels) expired, in
+ * which case that launch's output is incomplete.  Each plan owns one status word in a fixed
+ * device array of the library (nothing is allocated; at most 65536 plans and wave plans may
+ * be alive at once, more give STENCIL_ERR_OOM from stencil_plan); read it with the device that
+ * ran the plan current. */
 int stencil_sync_status(stencil_handle h, void *stream);
+
+/* stencil_set_wait_limit -- bound on every device-side wait of this plan's ring kernels
+ * (default 2 s; 0 < seconds <= 3600), and, for fault-injection tests only, a number of extra
+ * arrivals (0 .. 1000; 0 in normal use) that each ring slot's "consumers are done" barrier
+ * waits for and that never come.  With phantom_arrivals > 0, a launch whose CTAs walk more
+ * planes than the ring holds gives up after about `seconds`: the producer's wait for a free
+ * slot expires, every copy it issued still lands before its CTA exits, and the next
+ * stencil_sync_status returns STENCIL_ERR_TIMEOUT.  Takes effect at the next launch. */
+int stencil_set_wait_limit(stencil_handle h, double seconds, int phantom_arrivals);
 
 /* ---- batched sweeps (many grids, one persistent launch) ---------------------------------- */
 
@@ -249,7 +282,7 @@ uint64_t stencil_launch_count(void);
 const char *stencil_strerror(int code);
 
 /* stencil_abi_version -- ABI version of this header (STENCIL_ABI_VERSION). */
-#define STENCIL_ABI_VERSION 1
+#define STENCIL_ABI_VERSION 2
 int stencil_abi_version(void);
 
 #ifdef __cplusplus

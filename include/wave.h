@@ -61,6 +61,12 @@ int wave_misfit(wave_handle h, const float *traces, const float *observed, doubl
 int wave_gradient(wave_handle h, const float *v, const float *observed, float *traces,
                   double *J, double *g, void *stream);
 
+/* wave_sync_status -- synchronise `stream` and return the first error latched by a step
+ * kernel of this plan since the last call (STENCIL_ERR_TIMEOUT: a bounded device-side wait of
+ * the plane ring expired and the step's output is incomplete), then clear it.  Read it with
+ * the device that ran the plan current. */
+int wave_sync_status(wave_handle h, void *stream);
+
 /* wave_destroy -- free the plan and its device buffers (synchronises the device). */
 int wave_destroy(wave_handle h);
 

@@ -28,7 +28,9 @@ from .api import (  # noqa: F401
     stencil_offsets,
     stencil_plan,
     stencil_plan_get_variant,
+    stencil_plan_kernel_set,
     stencil_plan_set_variant,
+    stencil_set_wait_limit,
     stencil_size_class,
     stencil_strerror,
     stencil_sync_status,

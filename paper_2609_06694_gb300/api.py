@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-SHAPES = {"star": 0, "box": 1, "diamond": 2}
+SHAPES = {"star": 0, "box": 1, "diamond": 2, "custom": 3}
 DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
 BOUNDARIES = {"dirichlet": 0, "periodic": 1}
 KINDS = {"const": 0, "var": 1, "divkgrad": 2}
@@ -63,7 +63,9 @@ def _lib():
     lib = ctypes.CDLL(path)
     P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
     sig = {
-        "stencil_plan": ([ctypes.POINTER(P), I, P, I, I, I, P, I64, I, I], I),
+        "stencil_plan": ([ctypes.POINTER(P), I, P, I, I, I, P, I64, P, I, I], I),
+        "stencil_plan_kernel_set": ([P, P, P], I),
+        "stencil_set_wait_limit": ([P, ctypes.c_double, I], I),
         "stencil_offsets": ([P, P, I64, ctypes.POINTER(I64)], I),
         "stencil_destroy": ([P], I),
         "stencil_apply": ([P, P, P, I, P], I),
@@ -148,7 +150,9 @@ class Plan:
 
 
 def stencil_plan(ndim, dims, shape, radius, kind="const", coeffs=None, dtype="f32",
-                 boundary="dirichlet") -> Plan:
+                 boundary="dirichlet", offsets=None) -> Plan:
+    """shape "custom" takes `offsets`, an (n, ndim) integer array of distinct offsets (slowest
+    component first), with `coeffs` in the same order."""
     lib = _lib()
     d = (ctypes.c_int64 * ndim)(*[int(x) for x in dims])
     if coeffs is not None:
@@ -156,11 +160,28 @@ def stencil_plan(ndim, dims, shape, radius, kind="const", coeffs=None, dtype="f3
         cptr, n = c.ctypes.data_as(ctypes.c_void_p), len(c)
     else:
         c, cptr, n = None, None, 0
+    optr = None
+    if offsets is not None:
+        o = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, ndim)
+        optr = o.ctypes.data_as(ctypes.c_void_p)
     h = ctypes.c_void_p()
     rc = lib.stencil_plan(ctypes.byref(h), ndim, d, SHAPES[shape], int(radius), KINDS[kind], cptr,
-                          n, DTYPES[dtype], BOUNDARIES[boundary])
+                          n, optr, DTYPES[dtype], BOUNDARIES[boundary])
     _check(rc, "stencil_plan")
     return Plan(h.value, ndim, dims, shape, radius, kind, dtype, boundary)
+
+
+def stencil_plan_kernel_set(plan: Plan):
+    """(shape name, radius) of the compiled offset set the plan's kernels run."""
+    s, r = ctypes.c_int(), ctypes.c_int()
+    _check(_lib().stencil_plan_kernel_set(plan.handle, ctypes.byref(s), ctypes.byref(r)),
+           "stencil_plan_kernel_set")
+    return {v: k for k, v in SHAPES.items()}[s.value], r.value
+
+
+def stencil_set_wait_limit(plan: Plan, seconds: float, phantom_arrivals: int = 0):
+    _check(_lib().stencil_set_wait_limit(plan.handle, float(seconds), int(phantom_arrivals)),
+           "stencil_set_wait_limit")
 
 
 def stencil_offsets(plan: Plan) -> np.ndarray:

@@ -7,6 +7,26 @@
 
 namespace gst {
 
+// Bounds of the plane ring's device-side waits (a plan setting): every wait gives up after
+// `ns` nanoseconds (0 = the default of 2 s).  `phantom` > 0 adds that many arrivals that never
+// come to every slot's "consumers are done" barrier -- fault injection for tests only: the
+// producer's wait for a free slot then expires and the launch reports STENCIL_ERR_TIMEOUT,
+// while every copy already issued still lands before the CTA exits.
+struct RingWait {
+    unsigned long long ns = 0;
+    int phantom = 0;
+};
+
+// Device status words (status.cu): one per plan, in a fixed array of the library's device
+// image (nothing is allocated).  status_acquire returns a free slot or -1; status_word the
+// slot's device address on the current device (null if the lookup fails); status_take
+// synchronises the stream, then returns and clears the slot's code.
+constexpr int kStatusSlots = 65536;  // live plans at most (256 KiB per device)
+int status_acquire();
+void status_release(int slot, bool used);
+int *status_word(int slot);
+int status_take(int slot, cudaStream_t s);
+
 // One launch of the streaming sweep kernel (one time step).
 struct StreamLaunch {
     int ndim;                // 2 or 3
@@ -20,7 +40,8 @@ struct StreamLaunch {
     int stages = 0;          // ring depth (0 = fill the shared memory, see ring_stages)
     int z_lo = 0, z_hi = -1; // 3D: output planes [z_lo, z_hi) only (z_hi < 0: to nz)
     int use_tma = 1;         // 0 forces the cp.async loader (tensor maps are used when legal)
-    int *err;                // device error word or null
+    int *err = nullptr;      // device status word (status_word) or null
+    RingWait wait;           // bound on the ring's waits, fault injection
     cudaStream_t stream;
 };
 
@@ -81,6 +102,8 @@ struct VarLaunch {
     int narrays;
     int block_y, z_chunk;
     int vec_y = 1;  // div(k grad u): output rows per thread (1 or 2)
+    int *err = nullptr;  // device status word (div(k grad u), whose ring waits are bounded)
+    RingWait wait;
     cudaStream_t stream;
 };
 #define GST_DECLARE_VAR(DT)                               \

@@ -3,10 +3,9 @@
 //
 // stencil_apply ping-pongs between `out` and a grid-sized scratch buffer that the plan obtains
 // with cudaMalloc on its first multi-step call.  Some callers cannot let that happen: code
-// running inside a framework whose caching allocator owns (nearly) all device memory, code
-// that must not pay cudaMalloc's implicit device-wide synchronisation in a latency-critical
-// loop, or code that issues work while a stream is being captured (cudaMalloc is not
-// allowed during capture).  This entry point takes its scratch from a fixed array that lives
+// running inside a framework whose caching allocator owns (nearly) all device memory, or
+// code that must not pay cudaMalloc's implicit device-wide synchronisation in a
+// latency-critical loop.  This entry point takes its scratch from a fixed array that lives
 // in the library's own device image instead, so it allocates nothing.
 //
 // The array (STENCIL_NOALLOC_SCRATCH_BYTES = 16 MiB) exists once per GPU that loads the

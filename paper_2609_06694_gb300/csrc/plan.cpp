@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/stencil.h: plan validation, the dispatch map,
 // multi-step scheduling (ping-pong through a plan-owned scratch grid) and error reporting.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -228,8 +229,10 @@ static int launch_group(stencil_plan_s &p, const float *cf, const void *src, voi
     L.stages = v.stages;
     L.z_lo = z_lo;
     L.z_hi = z_hi;
-    L.err = nullptr;
+    L.err = status_word(p.status_slot);
+    L.wait = p.wait;
     L.stream = s;
+    p.launched = true;
     return map_launch_rc(launch_stream(L));
 }
 
@@ -380,7 +383,8 @@ const char *stencil_strerror(int code) {
 }
 
 int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, int radius,
-                 int kind, const double *coeffs, int64_t ncoeffs, int dtype, int boundary) {
+                 int kind, const double *coeffs, int64_t ncoeffs, const int32_t *custom_offsets,
+                 int dtype, int boundary) {
     // a dispatch map named by STENCIL_DISPATCH_MAP is read once, before the first plan
     static std::once_flag env_map_once;
     std::call_once(env_map_once, [] {
@@ -390,11 +394,12 @@ int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, 
     if (!out) return STENCIL_ERR_BADARG;
     *out = nullptr;
     if ((ndim != 2 && ndim != 3) || !dims) return STENCIL_ERR_BADARG;
-    if (shape < STENCIL_STAR || shape > STENCIL_DIAMOND) return STENCIL_ERR_BADARG;
+    if (shape < STENCIL_STAR || shape > STENCIL_CUSTOM) return STENCIL_ERR_BADARG;
     if (radius < 1 || radius > 4) return STENCIL_ERR_BADARG;
     if (dtype < STENCIL_F32 || dtype > STENCIL_BF16) return STENCIL_ERR_BADARG;
     if (boundary != STENCIL_DIRICHLET0 && boundary != STENCIL_PERIODIC) return STENCIL_ERR_BADARG;
     if (kind < STENCIL_CONST || kind > STENCIL_DIVKGRAD) return STENCIL_ERR_BADARG;
+    if ((shape == STENCIL_CUSTOM) != (custom_offsets != nullptr)) return STENCIL_ERR_BADARG;
     int64_t d[3] = {1, 1, 1};
     for (int i = 0; i < ndim; ++i) {
         if (dims[i] < 1) return STENCIL_ERR_BADARG;
@@ -402,7 +407,49 @@ int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, 
     }
     // kernels index one plane with 32-bit integers
     if (d[1] * d[2] > ((int64_t)1 << 30) || d[0] > ((int64_t)1 << 30)) return STENCIL_ERR_UNSUPPORTED;
-    std::vector<int32_t> offs = make_offsets(ndim, shape, radius);
+    // the offsets the caller sees (canonical order, or a custom set in the caller's order) and
+    // the compiled offset set the kernels run (the same, or the smallest compiled set that
+    // contains the custom one, its other offsets weighted 0)
+    std::vector<int32_t> offs;
+    int kshape = shape, kradius = radius;
+    if (shape == STENCIL_CUSTOM) {
+        if (kind != STENCIL_CONST) return STENCIL_ERR_UNSUPPORTED;
+        if (ncoeffs < 1 || ncoeffs > 729) return STENCIL_ERR_BADARG;
+        offs.assign(custom_offsets, custom_offsets + ncoeffs * ndim);
+        int rinf = 0, rl1 = 0;
+        bool axial = true;  // at most one nonzero component per offset
+        for (int64_t i = 0; i < ncoeffs; ++i) {
+            int nz = 0, l1 = 0;
+            for (int a = 0; a < ndim; ++a) {
+                const int c = offs[i * ndim + a];
+                if (c < -radius || c > radius) return STENCIL_ERR_BADARG;
+                nz += c != 0;
+                l1 += std::abs(c);
+                rinf = std::max(rinf, std::abs(c));
+            }
+            rl1 = std::max(rl1, l1);
+            axial = axial && nz <= 1;
+            for (int64_t j = 0; j < i; ++j)  // duplicates are an error
+                if (std::equal(offs.begin() + j * ndim, offs.begin() + (j + 1) * ndim,
+                               offs.begin() + i * ndim))
+                    return STENCIL_ERR_BADARG;
+        }
+        rinf = std::max(rinf, 1);
+        if (axial) {
+            kshape = STENCIL_STAR;
+            kradius = rinf;
+        } else {
+            kshape = STENCIL_BOX;
+            kradius = rinf;
+            if (rl1 <= 4 && make_offsets(ndim, STENCIL_DIAMOND, rl1).size() <
+                                make_offsets(ndim, STENCIL_BOX, rinf).size()) {
+                kshape = STENCIL_DIAMOND;
+                kradius = rl1;
+            }
+        }
+    } else {
+        offs = make_offsets(ndim, shape, radius);
+    }
     const int64_t npts = (int64_t)offs.size() / ndim;
     if (kind == STENCIL_CONST) {
         if (!coeffs || ncoeffs != npts) return STENCIL_ERR_BADARG;
@@ -415,12 +462,18 @@ int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, 
     }
     stencil_plan_s *p = new (std::nothrow) stencil_plan_s();
     if (!p) return STENCIL_ERR_OOM;
+    p->status_slot = status_acquire();  // host only: the word's address is looked up at launch
+    if (p->status_slot < 0) {
+        delete p;
+        return STENCIL_ERR_OOM;
+    }
     p->ndim = ndim;
     p->dims[0] = d[0];
     p->dims[1] = d[1];
     p->dims[2] = d[2];
-    p->shape = shape;
-    p->radius = radius;
+    p->shape = kshape;
+    p->radius = kradius;
+    p->custom = shape == STENCIL_CUSTOM;
     p->kind = kind;
     p->dtype = dtype;
     p->boundary = boundary;
@@ -428,15 +481,21 @@ int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, 
     p->offsets = offs;
     if (kind == STENCIL_CONST) {
         p->coeffs.assign(coeffs, coeffs + npts);
-        p->cf.resize(npts);
-        p->cf_flip.resize(npts);
-        for (int64_t i = 0; i < npts; ++i) p->cf[i] = (float)coeffs[i];
-        // flipped stencil: the coefficient of offset o moves to offset -o
-        for (int64_t i = 0; i < npts; ++i) {
+        // kernel coefficients over the compiled set, in its canonical order: the coefficient
+        // of each offset, and (adjoint) the coefficient of its negation; 0 where the plan's
+        // set has no such offset
+        const std::vector<int32_t> koffs = make_offsets(ndim, kshape, kradius);
+        const int64_t kn = (int64_t)koffs.size() / ndim;
+        p->cf.assign(kn, 0.0f);
+        p->cf_flip.assign(kn, 0.0f);
+        for (int64_t i = 0; i < kn; ++i) {
             for (int64_t j = 0; j < npts; ++j) {
-                bool neg = true;
-                for (int a = 0; a < ndim; ++a)
-                    if (offs[j * ndim + a] != -offs[i * ndim + a]) neg = false;
+                bool same = true, neg = true;
+                for (int a = 0; a < ndim; ++a) {
+                    if (offs[j * ndim + a] != koffs[i * ndim + a]) same = false;
+                    if (offs[j * ndim + a] != -koffs[i * ndim + a]) neg = false;
+                }
+                if (same) p->cf[i] = (float)coeffs[j];
                 if (neg) p->cf_flip[i] = (float)coeffs[j];
             }
         }
@@ -445,6 +504,13 @@ int stencil_plan(stencil_handle *out, int ndim, const int64_t *dims, int shape, 
     if (!lookup_map(*p, &v) || validate_variant(*p, v) != STENCIL_OK) v = default_variant(*p);
     p->variant = v;
     *out = p;
+    return STENCIL_OK;
+}
+
+int stencil_plan_kernel_set(stencil_handle h, int *shape, int *radius) {
+    if (!h) return STENCIL_ERR_BADARG;
+    if (shape) *shape = h->shape;
+    if (radius) *radius = h->radius;
     return STENCIL_OK;
 }
 
@@ -458,11 +524,12 @@ int stencil_offsets(stencil_handle h, int32_t *offsets_out, int64_t capacity, in
 
 int stencil_destroy(stencil_handle h) {
     if (!h) return STENCIL_OK;
-    if (h->scratch || h->stage_in || h->stage_out || h->d_err || h->s_in) cudaDeviceSynchronize();
+    if (h->scratch || h->stage_in || h->stage_out || h->launched || h->s_in)
+        cudaDeviceSynchronize();
+    status_release(h->status_slot, h->launched);
     if (h->scratch) cudaFree(h->scratch);
     if (h->stage_in) cudaFree(h->stage_in);
     if (h->stage_out) cudaFree(h->stage_out);
-    if (h->d_err) cudaFree(h->d_err);
     for (int i = 0; i < stencil_plan_s::kMaxSlabs; ++i) {
         if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
         if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
@@ -521,19 +588,16 @@ int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, in
 
 int stencil_sync_status(stencil_handle h, void *stream) {
     if (!h) return STENCIL_ERR_BADARG;
-    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-    if (e != cudaSuccess) return STENCIL_ERR_CUDA;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return STENCIL_ERR_CUDA;
-    if (h->d_err) {
-        int v = 0;
-        if (cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return STENCIL_ERR_CUDA;
-        if (v) {
-            cudaMemset(h->d_err, 0, sizeof(int));
-            return v;
-        }
-    }
+    return status_take(h->status_slot, (cudaStream_t)stream);
+}
+
+int stencil_set_wait_limit(stencil_handle h, double seconds, int phantom_arrivals) {
+    if (!h || !(seconds > 0.0) || seconds > 3600.0 || phantom_arrivals < 0 ||
+        phantom_arrivals > 1000)
+        return STENCIL_ERR_BADARG;
+    h->wait.ns = (unsigned long long)(seconds * 1e9);
+    if (h->wait.ns == 0) h->wait.ns = 1;
+    h->wait.phantom = phantom_arrivals;
     return STENCIL_OK;
 }
 
@@ -610,7 +674,10 @@ static int run_var_steps(stencil_plan_s &p, const void *in, const void *const *a
     L.block_y = p.variant.block_y;
     L.z_chunk = p.variant.z_chunk;
     L.vec_y = p.variant.vec_y;
+    L.err = status_word(p.status_slot);
+    L.wait = p.wait;
     L.stream = s;
+    p.launched = true;
     const void *src = in;
     for (int g = 0; g < steps; ++g) {
         void *dst = ((steps - 1 - g) % 2 == 0) ? out : p.scratch;

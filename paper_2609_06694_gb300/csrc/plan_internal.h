@@ -8,23 +8,27 @@
 #include <cuda_runtime.h>
 
 #include "../../include/stencil.h"
+#include "internal.h"
 
 struct stencil_plan_s {
     int ndim = 0;
     int64_t dims[3] = {1, 1, 1};  // (nz, ny, nx); nz = 1 for 2D grids
-    int shape = 0, radius = 0, kind = 0, dtype = 0, boundary = 0;
+    int shape = 0, radius = 0, kind = 0, dtype = 0, boundary = 0;  // shape, radius: compiled set
+    bool custom = false;           // a caller-given offset set (embedded in shape/radius)
     int64_t npts = 0;
-    std::vector<int32_t> offsets;  // npts * ndim, canonical order
+    std::vector<int32_t> offsets;  // npts * ndim, canonical order (custom: the caller's order)
     std::vector<double> coeffs;    // STENCIL_CONST: as given
-    std::vector<float> cf;         // f32 coefficients for the kernels
-    std::vector<float> cf_flip;    // coefficient of -o at index of o (adjoint)
+    std::vector<float> cf;         // f32 coefficients of the compiled set (0 where unused)
+    std::vector<float> cf_flip;    // coefficient of -o at the index of o (adjoint)
     stencil_variant variant{};
     void *scratch = nullptr;       // one grid of the storage type (multi-step ping-pong)
     size_t scratch_bytes = 0;
     void *stage_in = nullptr;      // staging for stencil_apply_host
     void *stage_out = nullptr;
     size_t stage_bytes = 0;
-    int *d_err = nullptr;          // device error word (allocated by the kernels that need one)
+    int status_slot = -1;          // the plan's device status word (status.cu)
+    bool launched = false;         // a kernel of this plan may have written the word
+    gst::RingWait wait;            // bound on the ring kernels' waits, fault injection
     // stencil_apply_host's z-slab pipeline: copy-in and copy-out streams and their events
     static constexpr int kMaxSlabs = 8;
     cudaStream_t s_in = nullptr, s_out = nullptr;

@@ -17,7 +17,7 @@ namespace gst {
 
 constexpr int kMaxStages = 16;   // ring slots
 constexpr int kMaxPatches = 256; // wrapped 16-byte chunks patched per plane
-constexpr unsigned long long kRingWaitNs = 2000000000ull;  // bounded waits: 2 s
+constexpr unsigned long long kRingWaitNs = 2000000000ull;  // default bound on a wait: 2 s
 
 // Shared-memory layout: nstage slots of NF fields, then full/empty/tma mbarriers, the abort
 // flag and the patch list.
@@ -49,9 +49,11 @@ struct Ring {
     uint32_t full_u32, empty_u32, tma_u32;
     volatile int *abort_flag;
     uint2 *plist;
+    unsigned long long limit_ns;  // bound on every wait
 
     __device__ __forceinline__ void setup(unsigned char *smem, uint32_t fbytes, int nf, int nstage,
-                                          uint32_t side_bytes = 0) {
+                                          unsigned long long wait_ns, uint32_t side_bytes = 0) {
+        limit_ns = wait_ns ? wait_ns : kRingWaitNs;
         base = smem;
         base_u32 = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
         field_bytes = fbytes;
@@ -64,11 +66,12 @@ struct Ring {
         abort_flag = reinterpret_cast<volatile int *>(smem + (size_t)ns * slot_bytes + 24 * ns);
         plist = reinterpret_cast<uint2 *>(smem + (size_t)ns * slot_bytes + 24 * ns + 16);
     }
-    // thread 0, before the CTA's only __syncthreads
-    __device__ __forceinline__ void init(int consumer_warps) const {
+    // thread 0, before the CTA's only __syncthreads.  `phantom` extra arrivals on the empty
+    // barriers never come (fault injection only: the producer's wait for a free slot expires).
+    __device__ __forceinline__ void init(int consumer_warps, int phantom = 0) const {
         for (int i = 0; i < ns; ++i) {
-            mbar_init(full_u32 + 8u * i, 32u);                       // the producer warp
-            mbar_init(empty_u32 + 8u * i, (uint32_t)consumer_warps);  // one per consumer warp
+            mbar_init(full_u32 + 8u * i, 32u);  // the producer warp
+            mbar_init(empty_u32 + 8u * i, (uint32_t)(consumer_warps + phantom));  // per warp
             mbar_init(tma_u32 + 8u * i, 1u);                         // the producer's lane 0
         }
         *abort_flag = 0;
@@ -80,7 +83,7 @@ struct Ring {
     // consumers: wait (warp-uniformly) for the plane in `slot`; false once a wait gives up
     __device__ __forceinline__ bool wait_full(int slot, uint32_t phase) const {
         return __all_sync(0xffffffffu, mbar_wait_abortable(full_u32 + 8u * slot, phase,
-                                                            kRingWaitNs, abort_flag));
+                                                            limit_ns, abort_flag));
     }
     // consumers: this warp has read `slot`
     __device__ __forceinline__ void release(int slot, int lane) const {
@@ -212,7 +215,7 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
     auto wait_all = [&](uint32_t bar, uint32_t parity) {
         // the lanes agree on the outcome, so the warp never splits
         return __all_sync(0xffffffffu,
-                          mbar_wait_abortable(bar, parity, kRingWaitNs, g.abort_flag));
+                          mbar_wait_abortable(bar, parity, g.limit_ns, g.abort_flag));
     };
     for (long long w = wk.w_first; w < wk.w_end && ok;) {
         const RingPiece q = wk.piece_at(w);
@@ -420,7 +423,7 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
                     if (idle++ == 0) t0 = globaltimer_ns();
                     else if ((idle & 63u) == 0 &&
                              __any_sync(0xffffffffu, *g.abort_flag != 0 ||
-                                                         globaltimer_ns() - t0 > kRingWaitNs)) {
+                                                         globaltimer_ns() - t0 > g.limit_ns)) {
                         ok = false;
                         break;
                     }

@@ -144,7 +144,9 @@ template <typename T> struct StreamParams {
     int use_side;       // 1 = x-wrapped halo chunks of edge tiles by side copies (periodic)
     int nstage;         // ring slots, 2 .. kMaxStages
     int z_lo, z_cnt;    // output planes [z_lo, z_lo + z_cnt) (3D; 0, 1 for 2D)
-    int *err;           // device error word (may be null)
+    int *err;           // device status word (may be null)
+    unsigned long long wait_ns;  // bound on the ring's waits (0: default)
+    int phantom;        // fault injection only: arrivals the empty barriers wait for in vain
 };
 
 // What happens to a finished output row segment (VY rows of VX cells at (zo, oy, ox)): the
@@ -273,8 +275,8 @@ __global__ void __launch_bounds__(
     const int TY = by * VY;
     const int rows = TY + 2 * R;
     Ring g;
-    g.setup(smem_raw, K::field_bytes(by), 1, p.nstage, K::side_bytes(by, SIDE));
-    if (tid == 0) g.init(ncons / 32);
+    g.setup(smem_raw, K::field_bytes(by), 1, p.nstage, p.wait_ns, K::side_bytes(by, SIDE));
+    if (tid == 0) g.init(ncons / 32, p.phantom);
     __syncthreads();  // the only CTA-wide barrier: from here on the warps meet at mbarriers
 
     const int nx = p.nx, ny = p.ny;

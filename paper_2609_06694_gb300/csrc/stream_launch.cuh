@@ -93,6 +93,8 @@ int launch_stream_t(const StreamLaunch &L,
     const bool ptr_ok = ((uintptr_t)L.in % 16 == 0) && ((uintptr_t)L.out % 16 == 0);
     p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
     p.err = L.err;
+    p.wait_ns = L.wait.ns;
+    p.phantom = L.wait.phantom;
 
     // Tensor-map (TMA) loads when rows are 16-byte aligned and the box fits the TMA limits
     // (the chunks a periodic grid wraps into an edge tile are filled inside the kernel).

@@ -316,7 +316,9 @@ template <typename T> struct DivkParams {
     int nx, ny, nz;
     int periodic, aligned, use_tma;
     int tiles_x, tiles_y, work, nstage;
-    int *err;
+    int *err;                    // device status word (may be null)
+    unsigned long long wait_ns;  // bound on the ring's waits (0: default)
+    int phantom;                 // fault injection only (see StreamParams)
 };
 
 // VY: output rows per consumer thread (1 or 2); two rows share one plane's wait, release and
@@ -348,8 +350,8 @@ __global__ void __launch_bounds__(DivkKernel<T, NDIM, VY>::MAX_THREADS + 32)
     const int tid = ty * BX + tx, ncons = BX * by, lane = tid & 31;
     const int TY = by * VY, rows = TY + 2 * R;
     Ring g;
-    g.setup(smem_raw, K::field_bytes(by), 2, p.nstage);
-    if (tid == 0) g.init(ncons / 32);
+    g.setup(smem_raw, K::field_bytes(by), 2, p.nstage, p.wait_ns);
+    if (tid == 0) g.init(ncons / 32, p.phantom);
     __syncthreads();  // the only CTA-wide barrier
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool periodic = p.periodic != 0, aligned = p.aligned != 0;

@@ -104,7 +104,9 @@ template <typename T, int NDIM, int VY> int launch_divkgrad_nd(const VarLaunch &
     p.aligned = (ptr_ok && (nx * (int64_t)sizeof(T)) % 16 == 0) ? 1 : 0;
     p.tiles_x = (int)((nx + K::TX - 1) / K::TX);
     p.tiles_y = (int)((ny + by * VY - 1) / (by * VY));
-    p.err = nullptr;
+    p.err = L.err;
+    p.wait_ns = L.wait.ns;
+    p.phantom = L.wait.phantom;
     const int rows = by * VY + 2;
     p.use_tma = (p.aligned &&
                  encode_plane_map<T>(&p.tmap[0], L.in, nx, ny, nz, K::PITCH, rows) &&

@@ -176,6 +176,8 @@ struct wave_plan_s {
     std::vector<float *> seg;                    // k fields: L u^n within a segment
     double *part = nullptr;
     int nparts = 0;
+    int status_slot = -1;   // device status word of the step kernels (status.cu)
+    bool launched = false;
 };
 
 static size_t wave_cells(const wave_plan_s *p) { return (size_t)p->nz * p->ny * p->nx; }
@@ -227,8 +229,9 @@ static int wave_step(wave_plan_s *p, bool adj, const float *u, const float *upre
     L.vec_y = 1;
     L.z_chunk = 64;
     L.stages = 4;
-    L.err = nullptr;
+    L.err = status_word(p->status_slot);
     L.stream = s;
+    p->launched = true;
     int rc;
     if (!adj) {
         const typename WaveEpi<false>::Params &ef = e;
@@ -322,6 +325,11 @@ int wave_plan(wave_handle *out, const int64_t *dims, int radius, const double *l
         return STENCIL_ERR_UNSUPPORTED;
     wave_plan_s *p = new (std::nothrow) wave_plan_s();
     if (!p) return STENCIL_ERR_OOM;
+    p->status_slot = status_acquire();
+    if (p->status_slot < 0) {
+        delete p;
+        return STENCIL_ERR_OOM;
+    }
     p->nz = dims[0];
     p->ny = dims[1];
     p->nx = dims[2];
@@ -413,9 +421,15 @@ int wave_gradient(wave_handle h, const float *v, const float *observed, float *t
     return cudaGetLastError() == cudaSuccess ? STENCIL_OK : STENCIL_ERR_CUDA;
 }
 
+int wave_sync_status(wave_handle h, void *stream) {
+    if (!h) return STENCIL_ERR_BADARG;
+    return status_take(h->status_slot, (cudaStream_t)stream);
+}
+
 int wave_destroy(wave_handle h) {
     if (!h) return STENCIL_OK;
     cudaDeviceSynchronize();
+    status_release(h->status_slot, h->launched);
     cudaFree(h->a);
     for (int i = 0; i < 3; ++i) {
         cudaFree(h->w[i]);

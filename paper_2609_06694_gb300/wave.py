@@ -23,6 +23,8 @@ def _wlib():
         lib.wave_gradient.restype = I
         lib.wave_destroy.argtypes = [P]
         lib.wave_destroy.restype = I
+        lib.wave_sync_status.argtypes = [P, P]
+        lib.wave_sync_status.restype = I
         lib._wave_sigs = True
     return lib
 
@@ -96,6 +98,10 @@ def wave_gradient(plan: WavePlan, v, observed, traces, J, g, stream=None):
                                  ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(g.data_ptr()),
                                  _stream_ptr(stream)), "wave_gradient")
     return J, g
+
+
+def wave_sync_status(plan: WavePlan, stream=None) -> int:
+    return _wlib().wave_sync_status(plan.handle, _stream_ptr(stream))
 
 
 def _autograd_classes():

@@ -47,7 +47,7 @@ def test_library_exports_every_declared_function():
 
 
 def test_abi_version_and_strerror():
-    assert gs.stencil_abi_version() == 1
+    assert gs.stencil_abi_version() == 2
     for code in (0, -1, -2, -3, -4, -5, -6):
         s = gs.stencil_strerror(code)
         assert s and s != "unknown status code"
@@ -77,7 +77,7 @@ def _plan_rc(ndim=3, dims=(8, 8, 8), shape=0, r=1, kind=0, coeffs="auto", dtype=
         coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
         cptr, n = coeffs.ctypes.data_as(ctypes.c_void_p), len(coeffs)
     h = ctypes.c_void_p()
-    rc = lib.stencil_plan(ctypes.byref(h), ndim, d, shape, r, kind, cptr, n, dtype, bc)
+    rc = lib.stencil_plan(ctypes.byref(h), ndim, d, shape, r, kind, cptr, n, None, dtype, bc)
     if h.value:
         lib.stencil_destroy(h)
     return rc
@@ -89,7 +89,8 @@ def test_plan_validation():
     assert _plan_rc(ndim=4, dims=(8, 8, 8, 8)) == -1
     assert _plan_rc(r=0) == -1
     assert _plan_rc(r=5) == -1
-    assert _plan_rc(shape=3) == -1
+    assert _plan_rc(shape=3) == -1                    # custom without its offsets
+    assert _plan_rc(shape=4) == -1
     assert _plan_rc(dtype=3) == -1
     assert _plan_rc(bc=2) == -1
     assert _plan_rc(kind=3) == -1
@@ -108,7 +109,69 @@ def test_plan_validation():
     assert _plan_rc(ndim=2, dims=(5, 7)) == 0
     assert _plan_rc(dims=(1, 1, 1)) == 0
     lib = api._lib()
-    assert lib.stencil_plan(None, 3, (ctypes.c_int64 * 3)(8, 8, 8), 0, 1, 0, None, 0, 0, 0) == -1
+    assert lib.stencil_plan(None, 3, (ctypes.c_int64 * 3)(8, 8, 8), 0, 1, 0, None, 0, None, 0,
+                            0) == -1
+
+
+def _custom_rc(offsets, ndim=3, r=2, kind=0, coeffs="auto", shape=3):
+    lib = api._lib()
+    d = (ctypes.c_int64 * ndim)(*([9] * ndim))
+    o = np.ascontiguousarray(offsets, dtype=np.int32)
+    n = len(o)
+    c = np.ones(n) if isinstance(coeffs, str) else coeffs
+    cptr = None if c is None else np.ascontiguousarray(c, dtype=np.float64).ctypes.data_as(
+        ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    rc = lib.stencil_plan(ctypes.byref(h), ndim, d, shape, r, kind, cptr,
+                          0 if c is None else len(c), o.ctypes.data_as(ctypes.c_void_p), 0, 0)
+    if h.value:
+        lib.stencil_destroy(h)
+    return rc
+
+
+def test_custom_offset_validation():
+    up = [(0, 0, 0), (0, 0, -1), (0, -1, 0), (-1, 0, 0), (0, 0, -2)]
+    assert _custom_rc(up) == 0
+    assert _custom_rc(up, r=1) == -1                       # |component| > radius
+    assert _custom_rc(up + [(0, 0, -1)]) == -1             # repeated offset
+    assert _custom_rc(up, coeffs=None) == -1               # ncoeffs = 0: no offsets, no weights
+    assert _custom_rc(up, kind=1, coeffs=None) == -2       # custom sets: constant weights only
+    assert _custom_rc(up, shape=0) == -1                   # offsets given for a named shape
+    assert _custom_rc([(0, 0, 5)], r=4) == -1
+    assert _custom_rc([(0, 0)], ndim=2, r=1) == 0
+    assert _custom_rc(np.zeros((0, 3)), r=1) == -1         # empty set
+
+
+@pytest.mark.parametrize("offsets,want", [
+    ([(0, 0, 0), (0, 0, -1), (0, 0, -2), (0, 1, 0), (3, 0, 0)], ("star", 3)),
+    ([(0, 0, 0)], ("star", 1)),
+    ([(1, 1, 0), (0, 0, 0), (-1, 0, 1)], ("diamond", 2)),    # 25 points < 27 of the box r1
+    ([(1, 1, 1), (0, 0, 0)], ("box", 1)),                    # diamond r3 (63) > box r1 (27)
+    ([(2, 2, 2), (0, 1, 0)], ("box", 2)),
+])
+def test_custom_sets_run_on_the_smallest_compiled_superset(offsets, want):
+    p = gs.stencil_plan(3, (9, 9, 9), "custom", 4, "const", np.arange(1.0, len(offsets) + 1),
+                        "f32", "periodic", offsets=offsets)
+    assert gs.stencil_plan_kernel_set(p) == want
+    # the plan reports the caller's offsets, in the caller's order
+    assert np.array_equal(gs.stencil_offsets(p), np.array(offsets, dtype=np.int32))
+
+
+def test_wait_limit_validation():
+    p = gs.stencil_plan(3, (8, 8, 8), "star", 1, "const", np.ones(7), "f32", "dirichlet")
+    gs.stencil_set_wait_limit(p, 0.5, 0)
+    for bad in ((0.0, 0), (-1.0, 0), (4000.0, 0), (1.0, -1), (1.0, 1001)):
+        with pytest.raises(gs.StencilError):
+            gs.stencil_set_wait_limit(p, *bad)
+
+
+def test_status_words_are_recycled():
+    # every plan takes one device status word from a fixed array; destroyed plans give theirs
+    # back, so creating and dropping many plans never runs out (host logic, no GPU needed)
+    for _ in range(3):
+        plans = [gs.stencil_plan(2, (8, 8), "star", 1, "const", np.ones(5), "f32", "dirichlet")
+                 for _ in range(30000)]
+        del plans
 
 
 def test_apply_argument_validation_needs_no_device():

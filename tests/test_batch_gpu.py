@@ -10,7 +10,8 @@ import torch
 
 import oracle
 import paper_2609_06694_gb300 as gs
-from helpers import TOL, make_input, oracle_run, relerr, seeded_weights
+from helpers import (TOL, check_steps, make_input, oracle_run, oracle_threads, relerr,
+                     seeded_weights)
 from paper_2609_06694_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -50,7 +51,8 @@ def test_mixed_batch_matches_oracle(steps):
     assert gs.stencil_batch_status(batch) == 0
     for g in grids:
         pure, emu = oracle_run(g["x64"], g["offs"], g["c"], g["bc"], steps, g["dtype"])
-        assert relerr(inputs.stored_values(g["yd"]), emu) < TOL[g["dtype"]]
+        check_steps(inputs.stored_values(g["yd"]), pure, emu, g["dtype"],
+                    f"batch {g['x64'].shape} x{steps}")
     # a second launch of the same graph gives the same result
     first = [g["yd"].clone() for g in grids]
     gs.stencil_batch_launch(batch)
@@ -90,8 +92,9 @@ def test_batch_rejects_unsupported_and_bad_items():
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_full_batch_256_grids_20_steps(dtype):
     """256 grids, sides log-uniform in [64, 2048] per axis, star r1/r2 and box 3x3/5x5, zero
-    Dirichlet, 20 steps: equal to 256 x 20 plain sweeps; grids small enough for the oracle are
-    also checked against it."""
+    Dirichlet, 20 steps, in the launch configuration the benchmark times: every grid against
+    the FP64 oracle (the tolerance holds against pure FP64; the error against the oracle that
+    rounds after every step is printed), and bit for bit equal to plain per-grid sweeps."""
     specs = inputs.batched_grid_specs()
     steps = 20
     rows = [(s["ny"], s["nx"], s["shape"], s["radius"], dtype, "dirichlet") for s in specs]
@@ -100,20 +103,20 @@ def test_full_batch_256_grids_20_steps(dtype):
     assert info["tiles"] > 256 and info["blocks"] >= 152
     gs.stencil_batch_launch(batch)
     assert gs.stencil_batch_status(batch) == 0
-    checked = 0
-    for g, s in zip(grids, specs):
-        ref = torch.empty_like(g["yd"])
-        gs.stencil_apply(g["plan"], g["xd"], ref, steps)
-        torch.cuda.synchronize()
-        assert torch.equal(ref, g["yd"])
-        if s["ny"] * s["nx"] <= 150 * 150 and checked < 6:
+    worst_pure = worst_emu = 0.0
+    with oracle_threads():
+        for g, s in zip(grids, specs):
+            ref = torch.empty_like(g["yd"])
+            gs.stencil_apply(g["plan"], g["xd"], ref, steps)
+            torch.cuda.synchronize()
+            assert torch.equal(ref, g["yd"])
             pure, emu = oracle_run(g["x64"], g["offs"], g["c"], "dirichlet", steps, dtype)
-            assert relerr(inputs.stored_values(g["yd"]), emu) < TOL[dtype]
-            err_pure = relerr(inputs.stored_values(g["yd"]), pure)
-            print(f"grid {s['ny']}x{s['nx']} {s['shape']} r{s['radius']} {dtype}: "
-                  f"err vs rounded-per-step oracle ok, vs pure FP64 {err_pure:.2e}")
-            checked += 1
-    assert checked >= 1
+            got = inputs.stored_values(g["yd"])
+            ep, ee = relerr(got, pure), relerr(got, emu)
+            assert ep < TOL[dtype], (s, ep)
+            worst_pure, worst_emu = max(worst_pure, ep), max(worst_emu, ee)
+    print(f"batched 256 grids x 20 steps {dtype}: worst max rel err {worst_pure:.2e} vs pure "
+          f"FP64, {worst_emu:.2e} vs per-step rounding")
 
 
 def test_barrier_timeout_is_reported_and_context_survives():

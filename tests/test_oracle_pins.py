@@ -147,6 +147,26 @@ def test_point_evaluation_is_the_sweep_at_every_cell(ndim, shape, r, bc):
         assert np.array_equal(got, oracle.sweep_const(x, offs, c, bc).ravel()[sel])
 
 
+@pytest.mark.parametrize("shape,r", [("star", 2), ("box", 1)])
+def test_dependency_slab_reproduces_the_periodic_sweep(shape, r):
+    """The slab the full-size GPU checks compare whole planes on: a Dirichlet run of the
+    periodically padded slab equals the periodic run on the middle plane, including grids
+    smaller than the slab (several wraps)."""
+    import sys
+    sys.path.insert(0, HERE)
+    from helpers import periodic_slab
+    offs = oracle.offsets(3, shape, r)
+    c = inputs.normalised_abs_weights(980, len(offs))
+    for dims, steps in (((12, 9, 10), 3), ((5, 4, 6), 2)):
+        x = inputs.uniform(981, dims)
+        full = oracle.run(x, "const", "periodic", steps, offs=offs, coeffs=c)
+        h = steps * r
+        for z0 in (0, dims[0] // 2, dims[0] - 1):
+            part = oracle.run(periodic_slab(x, z0, h), "const", "dirichlet", steps, offs=offs,
+                              coeffs=c)[h, h:-h, h:-h]
+            assert relerr(part, full[z0]) < 1e-13
+
+
 def test_threaded_build_gives_the_same_bits():
     """The OpenMP build of the oracle splits cell loops over threads only: every function used
     by the parity tests returns identical bits to the single-threaded build."""

@@ -4,9 +4,10 @@ Cases span every shape (star, box, diamond), radius 1-4, 2D and 3D grids, f32/f1
 storage and both boundary rules, on grids that cover several tiles plus ragged tails in x, y
 and z, on the vectorised (16-byte aligned rows) and scalar (odd row length) loaders, and the
 fused multi-step 2D kernel.  Tolerances: max-norm relative error 1e-5 (f32), 2e-3 (f16),
-1e-2 (bf16).  Multi-step low-precision runs are held to the same tolerance against the
-oracle that rounds to the storage type after every step (the library's stated semantics) and
-their error against pure FP64 is reported.
+1e-2 (bf16) against the FP64 oracle on the exact stored inputs.  Multi-step low-precision runs
+are held to the same tolerance against pure FP64 (no rounding between steps); their error
+against the oracle that rounds to the storage type after every step (the library's stated
+semantics) is printed as a diagnostic.
 """
 import numpy as np
 import pytest
@@ -14,7 +15,8 @@ import torch
 
 import oracle
 import paper_2609_06694_gb300 as gs
-from helpers import TOL, cone_reference, make_input, oracle_run, relerr, seeded_weights
+from helpers import (TOL, check_steps, make_input, oracle_run, oracle_threads, periodic_slab,
+                     relerr, seeded_weights)
 from paper_2609_06694_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -184,7 +186,7 @@ def test_apply_host_buffers(dtype, steps):
             torch.cuda.synchronize()
             assert torch.equal(hout, dev.cpu()), (dims, shape, bc, pinned)
         pure, emu = oracle_run(x64, offs, c, bc, steps, dtype)
-        assert relerr(inputs.stored_values(hout), emu) < TOL[dtype]
+        check_steps(inputs.stored_values(hout), pure, emu, dtype, f"host {dims} {shape}")
 
 
 def test_tiny_grids_wrap_many_times():
@@ -213,8 +215,7 @@ def test_multi_step_matches_oracle(ndim, shape, r, dtype, bc):
     x, x64 = make_input(62, dims, dtype)
     got = gpu_apply(plan, x, steps)
     pure, emu = oracle_run(x64, offs, c, bc, steps, dtype)
-    assert relerr(got, emu) < TOL[dtype]
-    assert relerr(got, pure) < 4 * TOL[dtype]
+    check_steps(got, pure, emu, dtype, f"{ndim}D {shape} r{r} {bc} x{steps}")
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -232,7 +233,7 @@ def test_fused2d_matches_oracle(shape, r, dtype, bc):
     steps = 7  # fused groups of 3, 3, 1
     got = gpu_apply(plan, x, steps)
     pure, emu = oracle_run(x64, offs, c, bc, steps, dtype)
-    assert relerr(got, emu) < TOL[dtype]
+    check_steps(got, pure, emu, dtype, f"fused 2D {shape} r{r} {bc} x{steps}")
 
 
 def test_fused_equals_unfused_bitwise():
@@ -291,10 +292,11 @@ def _laplacian_r4_plan(dims, bc="periodic"):
 
 
 @pytest.mark.parametrize("which", ["star4", "box27"])
-def test_full_size_512_cubed_samples(which):
-    """512^3 f32 periodic, in the launch configuration the benchmark times: 1 step checked at
-    sampled cells against the oracle's point evaluation, 8 steps at sampled cells through the
-    dependency cone."""
+def test_full_size_512_cubed_whole_grid(which):
+    """512^3 f32 periodic in the launch configuration the benchmark times: the 1-step result
+    against the oracle at every cell of the grid, and the 8-step result against the oracle at
+    every cell of five whole xy-planes (z = 0, 1, 255, 510, 511: the wrapped z ends, every tile
+    column with its wrapped x ends and patched y ends)."""
     dims = (512, 512, 512)
     if which == "star4":
         shape, r = "star", 4
@@ -315,16 +317,19 @@ def test_full_size_512_cubed_samples(which):
     gs.stencil_apply(plan, xd, y8, 8)
     assert gs.stencil_sync_status(plan) == 0
     x64 = inputs.stored_values(x)
-    rng = np.random.default_rng(5)
-    pts = [tuple(int(v) for v in rng.integers(0, 512, 3)) for _ in range(200)]
-    pts += [(0, 0, 0), (511, 511, 511), (0, 511, 3), (255, 0, 511)]
-    lin = [(p[0] * 512 + p[1]) * 512 + p[2] for p in pts]
-    ref1 = oracle.sweep_const_points(x64, offs, c, "periodic", lin)
-    got1 = y1.flatten()[torch.tensor(lin, device="cuda")].double().cpu().numpy()
-    assert relerr(got1, ref1) < 1e-5
-    scale1 = float(y1.abs().max())
-    assert np.max(np.abs(got1 - ref1)) / scale1 < 1e-5
-    sel = pts[:6]
-    ref8 = np.array([cone_reference(x64, offs, c, "periodic", 8, p) for p in sel])
-    got8 = np.array([float(y8[p]) for p in sel])
-    assert np.max(np.abs(got8 - ref8)) / float(y8.abs().max()) < 1e-5
+    with oracle_threads():
+        ref1 = oracle.sweep_const(x64, offs, c, "periodic")
+        err1 = relerr(inputs.stored_values(y1), ref1)
+        del ref1
+        h = 8 * r
+        errs = []
+        for z0 in (0, 1, 255, 510, 511):
+            ref = oracle.run(periodic_slab(x64, z0, h), "const", "dirichlet", 8, offs=offs,
+                             coeffs=c)[h, h:-h, h:-h]
+            got = y8[z0].double().cpu().numpy()
+            errs.append((np.max(np.abs(got - ref)), np.max(np.abs(ref))))
+    err8 = max(e for e, _ in errs) / max(m for _, m in errs)
+    print(f"512^3 {which}: 1 step max rel err {err1:.2e} (all cells); 8 steps {err8:.2e} "
+          f"(5 whole planes)")
+    assert err1 < 1e-5
+    assert err8 < 1e-5

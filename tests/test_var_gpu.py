@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import paper_2609_06694_gb300 as gs
-from helpers import TOL, make_input, relerr
+from helpers import TOL, check_steps, make_input, oracle_threads, relerr
 from paper_2609_06694_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -126,18 +126,19 @@ def test_divkgrad_small(ndim, dtype, bc):
     y2 = torch.empty_like(y)
     gs.stencil_apply_adjoint_var(plan, u.cuda(), [k.cuda()], y2, 1)
     assert torch.equal(y, y2)
-    # two steps against the oracle that rounds to storage between steps
+    # two steps: the tolerance against pure FP64, the per-step-rounded error printed
     gs.stencil_apply_var(plan, u.cuda(), [k.cuda()], y, 2)
+    pure = oracle.run(u64, "divkgrad", bc, 2, coeffs=k64)
     emu = oracle.run(u64, "divkgrad", bc, 2, coeffs=k64,
                      round_fmt="none" if dtype == "f32" else dtype)
-    assert relerr(inputs.stored_values(y), emu) < TOL[dtype]
+    check_steps(inputs.stored_values(y), pure, emu, dtype, f"div(k grad u) {ndim}D {bc} x2")
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_divkgrad_384_full_size_sampled(dtype):
-    """div(k grad u), 384^3, zero Dirichlet, in the launch configuration of the library's
-    defaults; a band of planes (including both z faces) checked against the oracle on the
-    exact stored inputs."""
+def test_divkgrad_384_full_size_whole_grid(dtype):
+    """div(k grad u), 384^3, zero Dirichlet, in the launch configuration the dispatch map
+    gives this size and storage type: every cell against the oracle on the exact stored
+    inputs; the max relative error is printed per storage type."""
     n = 384
     dims = (n, n, n)
     k = inputs.to_storage(inputs.lognormal_k(3002, dims), dtype)
@@ -146,16 +147,8 @@ def test_divkgrad_384_full_size_sampled(dtype):
     y = torch.empty_like(u, device="cuda")
     gs.stencil_apply_var(plan, u.cuda(), [k.cuda()], y, 1)
     assert gs.stencil_sync_status(plan) == 0
-    yh = inputs.stored_values(y)
-    k64, u64 = inputs.stored_values(k), inputs.stored_values(u)
-    errs = []
-    for z0 in (0, 190, n - 6):
-        lo, hi = max(0, z0 - 1), min(n, z0 + 7)
-        sub = oracle.divkgrad(u64[lo:hi], k64[lo:hi], "dirichlet")
-        # interior planes of the slab equal the full-grid result (slab faces see ghosts)
-        a = 0 if lo == 0 else 1
-        b = sub.shape[0] if hi == n else sub.shape[0] - 1
-        errs.append((np.max(np.abs(yh[lo + a:lo + b] - sub[a:b])), np.max(np.abs(sub[a:b]))))
-    err = max(e for e, _ in errs) / max(s for _, s in errs)
-    print(f"div(k grad u) 384^3 {dtype}: max relative error {err:.3e}")
+    with oracle_threads():
+        ref = oracle.divkgrad(inputs.stored_values(u), inputs.stored_values(k), "dirichlet")
+    err = relerr(inputs.stored_values(y), ref)
+    print(f"div(k grad u) 384^3 {dtype}: max relative error {err:.3e} (all cells)")
     assert err < TOL[dtype]

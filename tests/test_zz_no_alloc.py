@@ -1,6 +1,6 @@
 """GPU test of stencil_apply_noalloc, the sweep entry point for callers that may not allocate
-device memory (frameworks whose memory pool owns the GPU, latency-critical loops, work issued
-during stream capture).  Called directly through the C ABI, it must give the same result as
+device memory (frameworks whose memory pool owns the GPU, latency-critical loops that cannot
+absorb cudaMalloc's synchronisation).  Called directly through the C ABI, it must give the same result as
 stencil_apply on two calls in a row (the shared fixed scratch array keeps the previous call's
 contents, which must not matter), and must refuse a grid larger than its fixed scratch.
 
