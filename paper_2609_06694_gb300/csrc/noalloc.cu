@@ -68,9 +68,7 @@ extern "C" int stencil_apply_noalloc(stencil_handle h, const void *in, void *out
     rc = scratch_address(&scratch);
     if (rc) return rc;
     // the group schedule of stencil_apply: the last group writes `out`, `in` is never written
-    const int fuse = h->variant.family == STENCIL_FAMILY_FUSED2D
-                         ? (h->variant.fuse > 1 ? h->variant.fuse : 1)
-                         : 1;
+    const int fuse = gst::plan_steps_per_launch(*h);
     const int groups = (steps + fuse - 1) / fuse;
     const void *src = in;
     int done = 0;

@@ -48,5 +48,6 @@ int check_apply_args(const stencil_plan_s *p, const void *in, const void *out, i
 bool overlaps(const void *a, const void *b, size_t n);
 int launch_group_with(stencil_plan_s &p, const float *cf, const void *src, void *dst, int k,
                       cudaStream_t s);
+int plan_steps_per_launch(const stencil_plan_s &p);  // steps one launch of the plan fuses
 int map_launch_rc(int rc);
 }  // namespace gst

@@ -88,7 +88,12 @@ struct Ring {
     // consumers: this warp has read `slot`
     __device__ __forceinline__ void release(int slot, int lane) const {
         __syncwarp();
-        if (lane == 0) mbar_arrive(empty_u32 + 8u * slot);
+        // lane 0 arrives (a predicated arrive: no branch around it)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.eq.s32 p, %1, 0;\n"
+            " @p mbarrier.arrive.shared::cta.b64 _, [%0];\n}\n" ::"r"(empty_u32 + 8u * slot),
+            "r"(lane)
+            : "memory");
     }
     __device__ __forceinline__ void fail(int *err, int lane) const {
         *abort_flag = 1;

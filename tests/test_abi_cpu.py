@@ -337,3 +337,26 @@ def test_committed_dispatch_map_selects_its_entries():
         assert n >= 10
     finally:
         gs.stencil_load_dispatch_map(None)
+
+
+def test_fused3d_variant_validation():
+    f32 = dict(family=3, block_x=32, block_y=4, vec_y=2, z_chunk=16, fuse=2, tile_x=0,
+               tile_y=0, stages=0)
+    for shape, r, n in (("star", 1, 7), ("star", 2, 13), ("box", 1, 27), ("diamond", 2, 25)):
+        p = gs.stencil_plan(3, (64, 64, 64), shape, r, "const", np.ones(n), "f32", "periodic")
+        gs.stencil_plan_set_variant(p, **f32)
+        assert gs.stencil_plan_get_variant(p)["family"] == 3
+        for bad in (dict(fuse=3), dict(vec_y=1), dict(block_y=1), dict(block_y=8),
+                    dict(block_x=16)):
+            with pytest.raises(gs.StencilError):
+                gs.stencil_plan_set_variant(p, **dict(f32, **bad))
+    b = gs.stencil_plan(3, (64, 64, 64), "box", 1, "const", np.ones(27), "bf16", "dirichlet")
+    gs.stencil_plan_set_variant(b, **dict(f32, block_x=16, block_y=8, vec_y=1))
+    for shape, r, n in (("box", 2, 125), ("star", 3, 19)):
+        p = gs.stencil_plan(3, (64, 64, 64), shape, r, "const", np.ones(n), "f32", "periodic")
+        with pytest.raises(gs.StencilError) as e:
+            gs.stencil_plan_set_variant(p, **f32)
+        assert e.value.code == -2
+    p2 = gs.stencil_plan(2, (64, 64), "box", 1, "const", np.ones(9), "f32", "periodic")
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(p2, **f32)
