@@ -10,8 +10,12 @@ timed iterations.  Timing: W untimed warm-up steps, then K steps bracketed by a 
 torch.cuda.synchronize(), measured with CUDA events on the launching stream; the maximum over
 ranks is taken.  Several GPUs run independent replicas (weak scaling, no collective).
 
---impl reference times the FP64 oracle (single-threaded C) on the host on a bounded sample
-of the same workload; that is this project's reference arm.
+The same line carries `metric_ratios`: the adjoint against the forward sweep, div(k grad u)
+per storage type, the batched launch against plain per-grid sweeps and the wave gradient
+against its forward run, each with its own CUDA-event time (measured after the timed region).
+
+--impl reference times the FP64 oracle (its OpenMP build, every host core) on the host on a
+bounded sample of the same workload; that is this project's reference arm.
 """
 import argparse
 import json
@@ -304,6 +308,9 @@ def bench_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(W)
+    ratios = None
+    if rank == 0 and not args.no_ratios:
+        ratios = measure_metric_ratios(W)
 
     if world > 1:
         dist.barrier()
@@ -323,6 +330,7 @@ def bench_ours(args):
                     "api": "stencil_apply_host (pinned host buffers)"},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "metric_ratios": ratios,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -406,30 +414,46 @@ def _oracle_sample(seed_star=2001, seed_box=2003, nz=16):
     oracle.sweep_const(xb, offs_b, c_b, "periodic")
     dt = time.perf_counter() - t0
     desc = (f"one FP64 oracle sweep of the 25-pt star and of the 27-pt box on a {nz}x512x512 "
-            "periodic grid (same per-cell work as the 512^3 sweeps)")
+            f"periodic grid (same per-cell work as the 512^3 sweeps), {oracle.threads()} "
+            "host thread(s)")
     return 2 * nz * N * N, dt, desc
 
 
 def cpu_baseline_sample(W=None):
-    updates, dt, desc = _oracle_sample(nz=256)
-    return {"value": round(updates / dt / 1e9, 6), "unit": "Gcell-updates/s", "cores": 1,
-            "kind": "oracle", "sample": desc, "seconds": round(dt, 2)}
+    """The oracle on every host core (its OpenMP build: cell loops split over threads) over
+    the whole 512^3 grid, one sweep of each stencil; the single-thread rate on a 64-plane slab
+    is reported beside it."""
+    import oracle
+    oracle.use_threads(1)
+    u1, t1, _ = _oracle_sample(nz=64)
+    cores = oracle.use_threads(0)
+    try:
+        updates, dt, desc = _oracle_sample(nz=N)
+    finally:
+        oracle.use_threads(1)
+    return {"value": round(updates / dt / 1e9, 6), "unit": "Gcell-updates/s", "cores": cores,
+            "kind": "oracle", "sample": desc, "seconds": round(dt, 2),
+            "single_thread_value": round(u1 / t1 / 1e9, 6)}
 
 
 def bench_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on every host core (rank 0 only),
+    each step one sweep of each stencil on a 64 x 512 x 512 periodic slab."""
     rank, world, _ = rank_info()
     if rank != 0:
         return
     import oracle
     oracle.build()
+    cores = oracle.use_threads(0)
     for _ in range(args.warmup):
-        _oracle_sample(nz=2)
+        _oracle_sample(nz=16)
     total_u, total_t = 0, 0.0
     desc = None
     for _ in range(args.steps):
-        u, dt, desc = _oracle_sample(nz=2)
+        u, dt, desc = _oracle_sample(nz=64)
         total_u += u
         total_t += dt
+    oracle.use_threads(1)
     value = total_u / total_t / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 6),
@@ -438,7 +462,7 @@ def bench_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": [N, N, N], "boundary": "periodic",
                    "sample": desc},
-        "cpu_baseline": {"value": round(value, 6), "unit": "Gcell-updates/s", "cores": 1,
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gcell-updates/s", "cores": cores,
                          "kind": "oracle", "sample": desc},
         "e2e": {"value": round(value, 6), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -466,52 +490,49 @@ def _time(fn, reps=5, warm=2):
     return float(np.median(ts))
 
 
-def suite():
+def _frac(gbytes, ms, peak):
+    gbs = gbytes / (ms * 1e-3)
+    return round(gbs, 1), round(gbs / peak, 4)
+
+
+def measure_metric_ratios(W3=None, wave=True):
+    """The metric's other terms, measured on this GPU: the adjoint against the forward sweep
+    (512^3 star r4 and box, the 384^3 variable-coefficient star), div(k grad u) per storage
+    type, the batched launch against plain per-grid sweeps (256 grids x 20 steps, f32 and
+    bf16) and the wave-equation gradient against its forward run.  Every entry carries its own
+    CUDA-event median time and, where the bytes are fixed, its fraction of the measured HBM
+    copy rate.  Returns {name: entry}."""
     import torch
 
-    from paper_2609_06694_gb300 import build
-    build.build()
     import paper_2609_06694_gb300 as gs
     from paper_2609_06694_gb300 import inputs
-    from paper_2609_06694_gb300 import wave as W
+    from paper_2609_06694_gb300 import wave as WV
 
-    torch.cuda.set_device(0)
     peak, _ = measured_peaks()
-    out = []
-
-    # 2D 5-point Jacobi 512^2, 10 steps (L2-resident: latency-bound, reported formally vs HBM)
-    dims = (512, 512)
-    plan = gs.stencil_plan(2, dims, "star", 1, "const", np.full(5, 0.2), "f32", "dirichlet")
-    x = inputs.to_storage(inputs.uniform(1001, dims), "f32").cuda()
-    y = torch.empty_like(x)
-    ms = _time(lambda: gs.stencil_apply(plan, x, y, 10), reps=20)
-    out.append({"workload": "2D Jacobi 512^2 f32 Dirichlet, 10 steps", "ms": round(ms, 4),
-                "Gcell_updates_per_s": round(512 * 512 * 10 / ms / 1e6, 2),
-                "variant": gs.stencil_plan_get_variant(plan),
-                "note": "1 MiB grid stays in L2: latency-bound, not HBM-bound"})
-
-    # 3D 512^3 single and 8-step sweeps (the bench workload, per part), and the adjoint sweep
-    # (flipped coefficients through the same kernels) against the forward one
-    W3 = build_workload(torch.device("cuda", 0))
+    out = {}
+    own = W3 is None
+    if own:
+        W3 = build_workload(torch.device("cuda", torch.cuda.current_device()))
     for name, xin in (("star", "x_star"), ("box", "x_box")):
-        label = '25-pt star r4' if name == 'star' else '27-pt box'
-        for steps in (1, 8):
-            ms = _time(lambda: gs.stencil_apply(W3[name], W3[xin], W3["y"], steps))
-            gbs = 8 * CELLS * steps / (ms * 1e-3) / 1e9
-            out.append({"workload": f"3D 512^3 f32 periodic {label}, {steps} step(s)",
-                        "ms": round(ms, 4), "Gcell_updates_per_s": round(CELLS * steps / ms / 1e6, 2),
-                        "alg_GBps": round(gbs, 1), "frac_measured_hbm": round(gbs / peak, 4),
-                        "frac_nominal_8TBps": round(gbs / 8000.0, 4)})
         ms_f = _time(lambda: gs.stencil_apply(W3[name], W3[xin], W3["y"], 1))
         ms_a = _time(lambda: gs.stencil_apply_adjoint(W3[name], W3[xin], W3["y"], 1))
-        out.append({"workload": f"3D 512^3 f32 periodic {label}, adjoint vs forward sweep",
-                    "ms_forward": round(ms_f, 4), "ms_adjoint": round(ms_a, 4),
-                    "adjoint_over_forward": round(ms_a / ms_f, 3)})
-    del W3
-    torch.cuda.empty_cache()
+        gbs_f, fr_f = _frac(8 * CELLS / 1e9, ms_f, peak)
+        gbs_a, fr_a = _frac(8 * CELLS / 1e9, ms_a, peak)
+        out[f"adjoint_{name}_512"] = {
+            "workload": f"512^3 f32 periodic {'25-pt star r4' if name == 'star' else '27-pt box'}, "
+                        "1 sweep: adjoint (offset-flipped) vs forward",
+            "ms_forward": round(ms_f, 4), "ms_adjoint": round(ms_a, 4),
+            "adjoint_over_forward": round(ms_a / ms_f, 3),
+            "frac_hbm_forward": fr_f, "frac_hbm_adjoint": fr_a}
+        ms8 = _time(lambda: gs.stencil_apply(W3[name], W3[xin], W3["y"], 8), reps=3)
+        out[f"steps8_{name}_512"] = {
+            "workload": f"512^3 f32 periodic {name}, 8 steps", "ms": round(ms8, 4),
+            "Gcell_updates_per_s": round(CELLS * 8 / ms8 / 1e6, 2),
+            "frac_hbm": _frac(8 * 8 * CELLS / 1e9, ms8, peak)[1]}
+    if own:
+        del W3
+        torch.cuda.empty_cache()
 
-    # general variable coefficients (7 coefficient arrays, 3D star r1, 384^3): forward
-    # w_o[p] in[p+o] and adjoint w_o[q-o] in[q-o] (shifted gathers)
     n = 384
     for dt in ("f32", "bf16"):
         es = 4 if dt == "f32" else 2
@@ -522,38 +543,39 @@ def suite():
         ms_f = _time(lambda: gs.stencil_apply_var(plan, u, w, y, 1))
         ms_a = _time(lambda: gs.stencil_apply_adjoint_var(plan, u, w, y, 1))
         gb = 9 * es * n ** 3 / 1e9
-        out.append({"workload": f"variable-coefficient star r1 384^3 {dt} Dirichlet, forward / adjoint",
-                    "ms_forward": round(ms_f, 4), "ms_adjoint": round(ms_a, 4),
-                    "adjoint_over_forward": round(ms_a / ms_f, 3),
-                    "alg_GBps_forward": round(gb / (ms_f * 1e-3), 1),
-                    "frac_measured_hbm_forward": round(gb / (ms_f * 1e-3) / peak, 4),
-                    "frac_measured_hbm_adjoint": round(gb / (ms_a * 1e-3) / peak, 4)})
+        out[f"adjoint_var_star1_384_{dt}"] = {
+            "workload": f"variable-coefficient star r1 384^3 {dt} Dirichlet (7 coefficient "
+                        "arrays): adjoint (shifted gathers) vs forward",
+            "ms_forward": round(ms_f, 4), "ms_adjoint": round(ms_a, 4),
+            "adjoint_over_forward": round(ms_a / ms_f, 3),
+            "frac_hbm_forward": _frac(gb, ms_f, peak)[1],
+            "frac_hbm_adjoint": _frac(gb, ms_a, peak)[1]}
         del u, w, y
     torch.cuda.empty_cache()
 
-    # div(k grad u) 384^3 in three storage types
     kk = inputs.lognormal_k(3002, (n, n, n))
     uu = inputs.uniform(3001, (n, n, n))
     for dt in ("f32", "f16", "bf16"):
+        es = 4 if dt == "f32" else 2
         plan = gs.stencil_plan(3, (n, n, n), "star", 1, "divkgrad", None, dt, "dirichlet")
         k = inputs.to_storage(kk, dt).cuda()
         u = inputs.to_storage(uu, dt).cuda()
         y = torch.empty_like(u)
         ms = _time(lambda: gs.stencil_apply_var(plan, u, [k], y, 1))
-        es = 4 if dt == "f32" else 2
-        gbs = 3 * es * n ** 3 / (ms * 1e-3) / 1e9
-        out.append({"workload": f"div(k grad u) 384^3 {dt} Dirichlet, 1 step", "ms": round(ms, 4),
-                    "Gcell_updates_per_s": round(n ** 3 / ms / 1e6, 2), "alg_GBps": round(gbs, 1),
-                    "frac_measured_hbm": round(gbs / peak, 4)})
+        gbs, fr = _frac(3 * es * n ** 3 / 1e9, ms, peak)
+        out[f"divkgrad_384_{dt}"] = {
+            "workload": f"div(k grad u) 384^3 {dt} Dirichlet, 1 step", "ms": round(ms, 4),
+            "Gcell_updates_per_s": round(n ** 3 / ms / 1e6, 2), "alg_GBps": gbs,
+            "frac_hbm": fr}
         del k, u, y
+    del kk, uu
     torch.cuda.empty_cache()
 
-    # batched 2D: 256 grids, 20 steps, one persistent launch vs plain per-grid sweeps
     specs = inputs.batched_grid_specs()
     for dt in ("f32", "bf16"):
-        items, plans = [], []
+        items = []
         cells = 0
-        for i, sp in enumerate(specs):
+        for sp in specs:
             d = (sp["ny"], sp["nx"])
             npts = {"star": 4 * sp["radius"] + 1, "box": (2 * sp["radius"] + 1) ** 2}[sp["shape"]]
             c = inputs.normalised_abs_weights(sp["weight_seed"], npts)
@@ -569,50 +591,80 @@ def suite():
                 gs.stencil_apply(pl, xi, yi, 1)
 
         ms_1 = _time(plain_single_steps, reps=3, warm=1) * 20  # 256 x 20 single-step launches
-        ms_20 = _time(lambda: [gs.stencil_apply(pl, xi, yi, 20) for pl, xi, yi in items], reps=3,
-                      warm=1)
+        ms_20 = _time(lambda: [gs.stencil_apply(pl, xi, yi, 20) for pl, xi, yi in items],
+                      reps=3, warm=1)
         es = 4 if dt == "f32" else 2
-        gbs = 2 * es * cells * 20 / (ms_b * 1e-3) / 1e9
-        info = gs.stencil_batch_info(batch)
-        out.append({"workload": f"batched 2D, 256 grids, 20 steps, {dt}", "cells_per_step": cells,
-                    "ms_batched": round(ms_b, 3), "ms_plain_256x20_launches": round(ms_1, 3),
-                    "ms_plain_256_calls_of_20_steps": round(ms_20, 3),
-                    "speedup_vs_256x20": round(ms_1 / ms_b, 2),
-                    "speedup_vs_256_calls": round(ms_20 / ms_b, 2),
-                    "Gcell_updates_per_s": round(cells * 20 / ms_b / 1e6, 2),
-                    "alg_GBps": round(gbs, 1), "frac_measured_hbm": round(gbs / peak, 4),
-                    "batch": info})
+        gbs, fr = _frac(2 * es * cells * 20 / 1e9, ms_b, peak)
+        out[f"batched_256x20_{dt}"] = {
+            "workload": f"batched 2D, 256 grids (sides log-uniform 64-2048), 20 steps, {dt}, "
+                        "one persistent launch in a CUDA graph",
+            "cells_per_step": cells, "ms_batched": round(ms_b, 3),
+            "ms_plain_256x20_launches": round(ms_1, 3),
+            "ms_plain_256_calls_of_20_steps": round(ms_20, 3),
+            "batched_speedup_vs_256x20": round(ms_1 / ms_b, 2),
+            "batched_speedup_vs_256_calls": round(ms_20 / ms_b, 2),
+            "Gcell_updates_per_s": round(cells * 20 / ms_b / 1e6, 2), "alg_GBps": gbs,
+            "frac_hbm": fr, "batch": gs.stencil_batch_info(batch)}
         del batch, items
     torch.cuda.empty_cache()
 
-    # wave equation 256^3 x 500: forward, and gradient (forward + recompute + adjoint)
-    n3 = (256, 256, 256)
-    lap_plan = gs.stencil_plan(3, n3, "star", 4, "const", np.ones(25), "f32", "dirichlet")
-    lap = inputs.laplacian_coeffs(gs.stencil_offsets(lap_plan), 4)
-    h, steps = 10.0, 500
-    dt = 0.4 * h / 4500.0
-    wl = inputs.ricker(15.0, dt, steps)
-    v = inputs.velocity_field(5001, n3)
-    vt = inputs.perturbed_velocity(v)
-    wp = W.wave_plan(n3, 4, lap, h, dt, steps, (10, 128, 128), wl, 10, 25)
-    v32 = torch.from_numpy(v.astype(np.float32)).cuda()
-    vt32 = torch.from_numpy(vt.astype(np.float32)).cuda()
-    obs = torch.empty(wp.trace_shape, dtype=torch.float32, device="cuda")
-    W.wave_forward(wp, vt32, obs)
-    tr = torch.empty_like(obs)
-    J = torch.zeros(1, dtype=torch.float64, device="cuda")
-    g = torch.empty(n3, dtype=torch.float64, device="cuda")
-    ms_f = _time(lambda: W.wave_forward(wp, v32, tr), reps=3, warm=1)
-    ms_g = _time(lambda: W.wave_gradient(wp, v32, obs, tr, J, g), reps=3, warm=1)
-    cells = 256 ** 3
-    out.append({"workload": "3D acoustic wave 256^3, r4 Laplacian, 500 leapfrog steps",
-                "ms_forward": round(ms_f, 2), "ms_gradient": round(ms_g, 2),
-                "gradient_over_forward": round(ms_g / ms_f, 2),
-                "forward_Gcell_updates_per_s": round(cells * steps / ms_f / 1e6, 2),
-                "forward_alg_GBps": round(16 * cells * steps / (ms_f * 1e-3) / 1e9, 1),
-                "J": J.item(), "checkpoint_every": 25})
-    for row in out:
-        print(json.dumps(row), flush=True)
+    if wave:
+        n3 = (256, 256, 256)
+        lap_plan = gs.stencil_plan(3, n3, "star", 4, "const", np.ones(25), "f32", "dirichlet")
+        lap = inputs.laplacian_coeffs(gs.stencil_offsets(lap_plan), 4)
+        h, steps = 10.0, 500
+        dtw = 0.4 * h / 4500.0
+        wl = inputs.ricker(15.0, dtw, steps)
+        v = inputs.velocity_field(5001, n3)
+        vt = inputs.perturbed_velocity(v)
+        wp = WV.wave_plan(n3, 4, lap, h, dtw, steps, (10, 128, 128), wl, 10, 25)
+        v32 = torch.from_numpy(v.astype(np.float32)).cuda()
+        vt32 = torch.from_numpy(vt.astype(np.float32)).cuda()
+        obs = torch.empty(wp.trace_shape, dtype=torch.float32, device="cuda")
+        WV.wave_forward(wp, vt32, obs)
+        tr = torch.empty_like(obs)
+        J = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g = torch.empty(n3, dtype=torch.float64, device="cuda")
+        ms_f = _time(lambda: WV.wave_forward(wp, v32, tr), reps=3, warm=1)
+        ms_g = _time(lambda: WV.wave_gradient(wp, v32, obs, tr, J, g), reps=3, warm=1)
+        rc = WV.wave_sync_status(wp)
+        cells = 256 ** 3
+        out["wave_256_500"] = {
+            "workload": "3D acoustic wave 256^3, r4 Laplacian, 500 leapfrog steps; gradient by "
+                        "the adjoint with checkpoints every 25 steps (forward + recompute + "
+                        "adjoint, FP64 accumulation)",
+            "ms_forward": round(ms_f, 2), "ms_gradient": round(ms_g, 2),
+            "gradient_over_forward": round(ms_g / ms_f, 2),
+            "forward_Gcell_updates_per_s": round(cells * steps / ms_f / 1e6, 2),
+            "forward_frac_hbm": _frac(16 * cells * steps / 1e9, ms_f, peak)[1],
+            "status": rc}
+        del wp, v32, vt32, obs, tr, g
+        torch.cuda.empty_cache()
+    return out
+
+
+def suite():
+    import torch
+
+    from paper_2609_06694_gb300 import build
+    build.build()
+    import paper_2609_06694_gb300 as gs
+    from paper_2609_06694_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    # 2D 5-point Jacobi 512^2, 10 steps (L2-resident: latency-bound, reported formally vs HBM)
+    dims = (512, 512)
+    plan = gs.stencil_plan(2, dims, "star", 1, "const", np.full(5, 0.2), "f32", "dirichlet")
+    x = inputs.to_storage(inputs.uniform(1001, dims), "f32").cuda()
+    y = torch.empty_like(x)
+    ms = _time(lambda: gs.stencil_apply(plan, x, y, 10), reps=20)
+    print(json.dumps({"workload": "2D Jacobi 512^2 f32 Dirichlet, 10 steps", "ms": round(ms, 4),
+                      "Gcell_updates_per_s": round(512 * 512 * 10 / ms / 1e6, 2),
+                      "variant": gs.stencil_plan_get_variant(plan),
+                      "note": "1 MiB grid stays in L2: latency-bound, not HBM-bound"}),
+          flush=True)
+    for name, row in measure_metric_ratios().items():
+        print(json.dumps(dict(row, key=name)), flush=True)
 
 
 def main():
@@ -623,6 +675,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ratios", action="store_true",
+                    help="skip the adjoint / batched / div(k grad u) / wave measurements that "
+                         "the bench line carries under metric_ratios")
     ap.add_argument("--only", choices=["star", "box", "divkgrad", "var", "wave", "batch"],
                     default=None,
                     help="profiling case: only the 1-sweep call of one stencil, no JSON line")

@@ -129,6 +129,18 @@ int stencil_apply(stencil_handle h, const void *in, void *out, int steps, void *
  * (A^T y)[q] = sum_o c_o y[q - o], i.e. the stencil with every offset flipped. */
 int stencil_apply_adjoint(stencil_handle h, const void *in, void *out, int steps, void *stream);
 
+/* stencil_apply_reaction -- `steps` explicit steps of a reaction-diffusion equation whose
+ * spatial operator is the plan's sweep A, with the stencil and the pointwise physics fused in
+ * one launch per step (Sec. 4.3 fuses a stencil with an application's physics):
+ *     u^{t+1} = u^t + dt * ( (A u^t) + c1 u^t + c3 (u^t)^3 )
+ * (Allen-Cahn with a Laplacian A: c1 = 1/eps^2, c3 = -1/eps^2; c3 = 0: linear reaction).  In
+ * FP32 each cell computes fma(dt, fma(c3, u*u*u, fma(c1, u, L)), u) with L = (A u)[p], and
+ * rounds the result to the storage type.  STENCIL_CONST plans whose kernel set is a star of
+ * radius 1, 2 or 4 or the radius-1 box, f32 or bf16 storage (else UNSUPPORTED); dt, c1, c3
+ * finite (else BADARG); `in`, `out`, `steps`, scratch and errors as stencil_apply. */
+int stencil_apply_reaction(stencil_handle h, const void *in, void *out, int steps, double dt,
+                           double c1, double c3, void *stream);
+
 /* stencil_apply_var -- sweeps of a STENCIL_VAR or STENCIL_DIVKGRAD plan.
  *   VAR:      coeff_arrays[npts] are device pointers to grid-shaped arrays of the storage
  *             type; out[p] = sum_o coeff_arrays[o][p] * in[p + o]  (Sec. 2.1).
@@ -255,6 +267,12 @@ typedef struct {
 #define STENCIL_FAMILY_STREAM 1 /* one sweep per launch, z-streaming tiles on a plane ring fed
                                    by a producer warp (tensor copies)                        */
 #define STENCIL_FAMILY_FUSED2D 2 /* several 2D sweeps per launch in a shared-memory tile      */
+#define STENCIL_FAMILY_FUSED3D 3 /* two 3D sweeps per launch on the plane ring (temporal
+                                    blocking, Sec. 4.3): the intermediate plane stays in shared
+                                    memory; star/diamond radius 1-2 and the radius-1 box; fuse
+                                    must be 2, vec_y 2 (f32) or 1 (16-bit storage), block_y
+                                    >= 2 * radius; an odd last step runs on the streaming
+                                    kernel                                                     */
 
 /* stencil_plan_get_variant / stencil_plan_set_variant -- read or override the kernel variant
  * a plan uses (the autotuner's knob).  set validates the variant against the plan and returns

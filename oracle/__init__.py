@@ -98,6 +98,8 @@ def _open(path):
         lib.orc_misfit.restype = D
         lib.orc_wave_gradient.argtypes = [P, I64, P, P, P, D, D, I, I64, P, I64, P, I, P, P]
         lib.orc_wave_gradient.restype = I
+        lib.orc_reaction_run.argtypes = [I, P, I64, P, P, I, I, D, D, D, I, P, P]
+        lib.orc_reaction_run.restype = I
         lib.orc_set_threads.argtypes = [I]
         lib.orc_set_threads.restype = I
         _libs[path] = lib
@@ -238,6 +240,21 @@ def run(x, kind, bc, steps, *, offs=None, coeffs=None, adjoint=False, round_fmt=
                       _ptr(out))
     if rc != 0:
         raise RuntimeError(f"orc_run failed: {rc}")
+    return out
+
+
+def reaction(x, offs, coeffs, bc, steps, dt, c1, c3, round_fmt="none"):
+    """``steps`` reaction-diffusion steps u + dt (A u + c1 u + c3 u^3), rounding to
+    ``round_fmt`` after each step."""
+    x = _f64(x)
+    offs = np.ascontiguousarray(offs, dtype=np.int32)
+    c = _f64(coeffs)
+    out = np.empty_like(x)
+    rc = _L().orc_reaction_run(x.ndim, _ptr(_dims(x.shape)), len(offs), _ptr(offs), _ptr(c),
+                               _bc(bc), int(steps), float(dt), float(c1), float(c3),
+                               ROUND[round_fmt], _ptr(x), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("orc_reaction_run failed")
     return out
 
 

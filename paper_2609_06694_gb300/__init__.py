@@ -7,6 +7,7 @@ library raises instead of falling back to anything else.
 """
 from .api import (  # noqa: F401
     FAMILY_FUSED2D,
+    FAMILY_FUSED3D,
     FAMILY_STREAM,
     Batch,
     Plan,
@@ -17,6 +18,7 @@ from .api import (  # noqa: F401
     stencil_apply_adjoint,
     stencil_apply_adjoint_var,
     stencil_apply_host,
+    stencil_apply_reaction,
     stencil_apply_var,
     stencil_batch_info,
     stencil_batch_launch,

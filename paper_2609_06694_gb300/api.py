@@ -20,6 +20,7 @@ BOUNDARIES = {"dirichlet": 0, "periodic": 1}
 KINDS = {"const": 0, "var": 1, "divkgrad": 2}
 FAMILY_STREAM = 1
 FAMILY_FUSED2D = 2
+FAMILY_FUSED3D = 3
 
 _ERRORS = {-1: "BADARG", -2: "UNSUPPORTED", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "BOUNDS"}
 
@@ -66,6 +67,8 @@ def _lib():
         "stencil_plan": ([ctypes.POINTER(P), I, P, I, I, I, P, I64, P, I, I], I),
         "stencil_plan_kernel_set": ([P, P, P], I),
         "stencil_set_wait_limit": ([P, ctypes.c_double, I], I),
+        "stencil_apply_reaction": ([P, P, P, I, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, P], I),
         "stencil_offsets": ([P, P, I64, ctypes.POINTER(I64)], I),
         "stencil_destroy": ([P], I),
         "stencil_apply": ([P, P, P, I, P], I),
@@ -177,6 +180,17 @@ def stencil_plan_kernel_set(plan: Plan):
     _check(_lib().stencil_plan_kernel_set(plan.handle, ctypes.byref(s), ctypes.byref(r)),
            "stencil_plan_kernel_set")
     return {v: k for k, v in SHAPES.items()}[s.value], r.value
+
+
+def stencil_apply_reaction(plan: Plan, inp, out, steps, dt, c1, c3, stream=None):
+    """`steps` fused reaction-diffusion steps u + dt (A u + c1 u + c3 u^3)."""
+    plan._check_tensor(inp, "in")
+    plan._check_tensor(out, "out")
+    _check(_lib().stencil_apply_reaction(plan.handle, ctypes.c_void_p(inp.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), int(steps), float(dt),
+                                         float(c1), float(c3), _stream_ptr(stream)),
+           "stencil_apply_reaction")
+    return out
 
 
 def stencil_set_wait_limit(plan: Plan, seconds: float, phantom_arrivals: int = 0):

@@ -74,6 +74,19 @@ constexpr bool stream_vy_compiled(int ndim, int shape, int radius, int vec_y) {
            (vec_y == 4 && radius == 1);
 }
 
+// Two time steps of a 3D stencil in one launch (fused3d.cuh): the StreamLaunch fields as for
+// the streaming kernel (block_y rows of threads, vec_y must be 2); compiled for star and
+// diamond sets of radius 1-2 and the radius-1 box.
+int launch_fused3d(const StreamLaunch &L);
+
+// One reaction-diffusion step u + dt (A u + c1 u + c3 u^3) on the streaming kernel (reaction.cuh):
+// vec_y must be 1; star sets of radius 1, 2, 4 and the radius-1 box; f32 and bf16 storage.
+int launch_reaction_f32(const StreamLaunch &L, float dt, float c1, float c3);
+int launch_reaction_bf16(const StreamLaunch &L, float dt, float c1, float c3);
+constexpr bool fused3d_compiled(int ndim, int shape, int radius) {
+    return ndim == 3 && ((shape != 1 && radius >= 1 && radius <= 2) || (shape == 1 && radius == 1));
+}
+
 // Several 2D time steps in one launch (shared-memory tile with a shrinking halo).
 struct Fused2DLaunch {
     int64_t ny, nx;

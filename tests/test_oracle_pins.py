@@ -167,6 +167,53 @@ def test_dependency_slab_reproduces_the_periodic_sweep(shape, r):
             assert relerr(part, full[z0]) < 1e-13
 
 
+# --------------------------------------------------------------------------------------------
+# reaction-diffusion (stencil fused with pointwise physics)
+# --------------------------------------------------------------------------------------------
+
+def test_reaction_without_diffusion_is_a_scalar_ode_per_cell():
+    """Zero weights: every cell follows explicit Euler for u' = c1 u + c3 u^3 on its own,
+    computed here cell by cell in plain Python with the same FP64 operations."""
+    offs = oracle.offsets(3, "star", 2)
+    x = inputs.uniform(990, (4, 5, 6))
+    dt, c1, c3, steps = 0.05, 3.0, -2.5, 7
+    got = oracle.reaction(x, offs, np.zeros(len(offs)), "periodic", steps, dt, c1, c3)
+    for idx in ((0, 0, 0), (3, 4, 5), (2, 1, 3)):
+        u = float(x[idx])
+        for _ in range(steps):
+            u = u + dt * (0.0 + c1 * u + c3 * u * u * u)
+        assert got[idx] == u
+
+
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+def test_reaction_linear_part_is_the_sweep_of_identity_plus_dt_a(bc):
+    """c1 = c3 = 0: one step is the sweep with weights dt * c and 1 added at the centre."""
+    offs = oracle.offsets(3, "box", 1)
+    c = inputs.uniform(991, (len(offs),))
+    x = inputs.uniform(992, (6, 7, 8))
+    dt = 0.3
+    w = dt * c
+    w[[i for i, o in enumerate(offs) if not np.any(o)][0]] += 1.0
+    want = oracle.run(x, "const", bc, 2, offs=offs, coeffs=w)
+    got = oracle.reaction(x, offs, c, bc, 2, dt, 0.0, 0.0)
+    assert relerr(got, want) < 1e-13
+
+
+def test_reaction_constant_field_closed_form():
+    """A constant field on a periodic grid stays constant: u <- u + dt (u sum(c) + c1 u +
+    c3 u^3), iterated as a scalar recurrence; the linear reaction term c1 shifts it as a
+    weight on the centre would."""
+    offs = oracle.offsets(2, "star", 1)
+    c = np.array([0.5, 1.0, -4.0, 1.0, 0.25])
+    dt, c1, c3 = 0.01, 2.0, -1.0
+    x = np.full((9, 11), 0.3)
+    got = oracle.reaction(x, offs, c, "periodic", 5, dt, c1, c3)
+    u = 0.3
+    for _ in range(5):
+        u = u + dt * (u * np.sum(c) + c1 * u + c3 * u ** 3)
+    assert relerr(got, np.full_like(x, u)) < 1e-14
+
+
 def test_threaded_build_gives_the_same_bits():
     """The OpenMP build of the oracle splits cell loops over threads only: every function used
     by the parity tests returns identical bits to the single-threaded build."""
