@@ -529,6 +529,38 @@ def measure_metric_ratios(W3=None, wave=True):
             "workload": f"512^3 f32 periodic {name}, 8 steps", "ms": round(ms8, 4),
             "Gcell_updates_per_s": round(CELLS * 8 / ms8 / 1e6, 2),
             "frac_hbm": _frac(8 * 8 * CELLS / 1e9, ms8, peak)[1]}
+    # temporal blocking in 3D: 8 steps as four fused pairs against eight single sweeps, and
+    # the reaction-diffusion step (stencil + pointwise physics in one launch) against the plain
+    # sweep of the same stencil
+    dims = (N, N, N)
+    c7 = np.array([1.0, 1.0, 1.0, -6.0, 1.0, 1.0, 1.0]) / 6.0
+    c27, _ = inputs.normalised_sum_weights(2002, 27)
+    for name, shape, c, by in (("star1", "star", c7, 7), ("box", "box", c27, 7)):
+        plain = gs.stencil_plan(3, dims, shape, 1, "const", c, "f32", "periodic")
+        gs.stencil_plan_set_variant(plain, family=gs.FAMILY_STREAM)
+        fused = gs.stencil_plan(3, dims, shape, 1, "const", c, "f32", "periodic")
+        gs.stencil_plan_set_variant(fused, family=gs.FAMILY_FUSED3D, block_x=32, block_y=by,
+                                    vec_y=2, z_chunk=64, fuse=2, tile_x=0, tile_y=0, stages=0)
+        ms_p = _time(lambda: gs.stencil_apply(plain, W3["x_box"], W3["y"], 8), reps=3)
+        ms_f = _time(lambda: gs.stencil_apply(fused, W3["x_box"], W3["y"], 8), reps=3)
+        out[f"fused3d_{name}_512_8steps"] = {
+            "workload": f"512^3 f32 periodic {shape} r1, 8 steps: four two-step fused launches "
+                        "vs eight single sweeps",
+            "ms_single_sweeps": round(ms_p, 4), "ms_fused_pairs": round(ms_f, 4),
+            "fused_speedup": round(ms_p / ms_f, 3),
+            "frac_hbm_single": _frac(8 * 8 * CELLS / 1e9, ms_p, peak)[1],
+            "frac_hbm_fused_equivalent": _frac(8 * 8 * CELLS / 1e9, ms_f, peak)[1]}
+        if name == "star1":
+            ms_1 = _time(lambda: gs.stencil_apply(plain, W3["x_box"], W3["y"], 1))
+            ms_r = _time(lambda: gs.stencil_apply_reaction(plain, W3["x_box"], W3["y"], 1, 0.1,
+                                                           1.0, -1.0))
+            out["reaction_star1_512"] = {
+                "workload": "512^3 f32 periodic Allen-Cahn step u + dt (L u + u - u^3), 7-point "
+                            "Laplacian, fused in one launch, vs the plain sweep",
+                "ms_sweep": round(ms_1, 4), "ms_reaction_step": round(ms_r, 4),
+                "reaction_over_sweep": round(ms_r / ms_1, 3),
+                "frac_hbm_reaction": _frac(8 * CELLS / 1e9, ms_r, peak)[1]}
+        del plain, fused
     if own:
         del W3
         torch.cuda.empty_cache()

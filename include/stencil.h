@@ -281,15 +281,21 @@ int stencil_plan_get_variant(stencil_handle h, stencil_variant *v);
 int stencil_plan_set_variant(stencil_handle h, const stencil_variant *v);
 
 /* stencil_load_dispatch_map -- replace the process-wide dispatch map with the one in the
- * text file at `path` (format: lines "ndim shape radius dtype boundary kind size_class :
- * family block_x block_y vec_y z_chunk fuse tile_x tile_y [stages]", '#' comments; a
- * missing stages field reads as 0).  Plans created
+ * text file at `path` (format: lines "ndim shape radius dtype boundary kind size_class
+ * [geometry] : family block_x block_y vec_y z_chunk fuse tile_x tile_y [stages]", '#'
+ * comments; a key field of -1 matches anything, a missing geometry field reads as -1 and a
+ * missing stages field as 0; the first matching line wins).  Plans created
  * afterwards use it.  NULL restores the built-in defaults.  If the environment variable
  * STENCIL_DISPATCH_MAP names a file, it is loaded once before the first stencil_plan. */
 int stencil_load_dispatch_map(const char *path);
 
 /* stencil_size_class -- the size class (0 .. 3) a grid of `cells` cells falls in. */
 int stencil_size_class(int64_t cells);
+
+/* stencil_geometry_class -- the geometry class of a grid in the dispatch key (Sec. 4.3: the
+ * kernel is specialised per grid shape): 1 for a 3D slab thin in z (nz * 8 <= ny and
+ * nz * 8 <= nx), 0 otherwise (cube-like 3D grids, every 2D grid).  dims as in stencil_plan. */
+int stencil_geometry_class(int ndim, const int64_t *dims);
 
 /* ---- introspection ----------------------------------------------------------------------- */
 

@@ -25,6 +25,7 @@ from .api import (  # noqa: F401
     stencil_batch_plan,
     stencil_batch_set_wait_limit,
     stencil_batch_status,
+    stencil_geometry_class,
     stencil_launch_count,
     stencil_load_dispatch_map,
     stencil_offsets,

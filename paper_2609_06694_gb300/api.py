@@ -87,6 +87,7 @@ def _lib():
         "stencil_plan_set_variant": ([P, ctypes.POINTER(stencil_variant)], I),
         "stencil_load_dispatch_map": ([ctypes.c_char_p], I),
         "stencil_size_class": ([I64], I),
+        "stencil_geometry_class": ([I, P], I),
         "stencil_launch_count": ([], ctypes.c_uint64),
         "stencil_strerror": ([I], ctypes.c_char_p),
         "stencil_abi_version": ([], I),
@@ -293,6 +294,13 @@ def stencil_load_dispatch_map(path):
 
 def stencil_size_class(cells: int) -> int:
     return _lib().stencil_size_class(int(cells))
+
+
+def stencil_geometry_class(ndim: int, dims) -> int:
+    d = (ctypes.c_int64 * ndim)(*[int(x) for x in dims])
+    rc = _lib().stencil_geometry_class(int(ndim), d)
+    _check(min(rc, 0), "stencil_geometry_class")
+    return rc
 
 
 def stencil_launch_count() -> int:

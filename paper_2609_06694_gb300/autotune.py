@@ -1,13 +1,16 @@
 """Autotuner that fills the dispatch map (ForgeStencil Sec. 4.3: the kernel is specialised per
 stencil type, grid shape and precision; here the specialisation is chosen by measurement).
 
-For each tuning key (ndim, shape, radius, dtype, boundary, kind, size class) it times every
-candidate kernel variant on a representative grid with CUDA events (median of several runs,
-inputs larger than L2 for the 3D cases), and records the fastest together with its achieved
-bandwidth (algorithmic bytes / time) and fraction of the measured HBM peak.  The result is a
-text map read by ``stencil_load_dispatch_map`` (one line per key) plus a JSON evidence file.
+For each tuning key (ndim, shape, radius, dtype, boundary, kind, size class, geometry class)
+it times every candidate kernel variant on a representative grid with CUDA events (median of
+several runs, inputs larger than L2 for the 3D cases) -- streaming tiles, ring depths and z
+chunks, fused 2D depths and tiles, and for the small 3D offset sets the two-step fused 3D
+kernel against single sweeps over 8 steps -- and records the fastest with its algorithmic
+bandwidth.  Each winner is then captured once under ncu (DRAM bytes read and written, device
+time), so the evidence shows the bytes the kernel really moved.  The result is a text map read
+by ``stencil_load_dispatch_map`` (one line per key) plus a JSON evidence file.
 
-Usage on a GPU:  python -m paper_2609_06694_gb300.autotune [--out DIR] [--quick]
+Usage on a GPU:  python -m paper_2609_06694_gb300.autotune [--out MAP] [--quick] [--no-ncu]
 """
 from __future__ import annotations
 
@@ -108,26 +111,52 @@ def divkgrad_candidates(dtype, quick=False):
     return out
 
 
-def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=print,
-             kind="const"):
-    """Time every candidate on `dims`; returns (best_variant, evidence list)."""
+def fused3d_candidates(shape, radius, dtype, quick=False):
+    """Two-step fused 3D variants (temporal blocking): rows of threads, z chunk, ring depth."""
+    bx = 32 if dtype == "f32" else 16
+    vy = 2 if dtype == "f32" else 1
+    out = []
+    heights = (4, 7) if quick else (2, 4, 5, 6, 7) if bx == 32 else (8, 10, 12, 14)
+    for by, zc, ns in itertools.product(heights, (32, 64), (0, 3, 6)):
+        if by < 2 * radius or bx * by > 224 or (bx * by) % 32:
+            continue
+        out.append(dict(family=gs.FAMILY_FUSED3D, block_x=bx, block_y=by, vec_y=vy, z_chunk=zc,
+                        fuse=2, tile_x=0, tile_y=0, stages=ns))
+    return out
+
+
+FUSED3D_SETS = {("star", 1), ("star", 2), ("diamond", 1), ("diamond", 2), ("box", 1)}
+
+
+def _problem(ndim, dims, shape, radius, dtype, bc, kind):
+    """(plan, run(plan, steps), bytes per cell and step, candidates) of a tuning key."""
     import torch
     x = inputs.to_storage(inputs.uniform(8, dims), dtype).cuda()
     y = torch.empty_like(x)
     if kind == "divkgrad":
         plan = gs.stencil_plan(ndim, dims, "star", 1, "divkgrad", None, dtype, bc)
         k = inputs.to_storage(inputs.lognormal_k(4, dims), dtype).cuda()
+        return plan, (lambda p, n: gs.stencil_apply_var(p, x, [k], y, n)), 3
+    c = inputs.normalised_abs_weights(7, _npts(ndim, shape, radius))
+    plan = gs.stencil_plan(ndim, dims, shape, radius, "const", c, dtype, bc)
+    return plan, (lambda p, n: gs.stencil_apply(p, x, y, n)), 2
+
+
+def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=print,
+             kind="const"):
+    """Time every candidate on `dims`; returns (best_variant, evidence list).  For offset sets
+    the fused 3D kernel covers, the key is timed over 8 steps so that the two-step fused
+    launches compete with eight single sweeps."""
+    plan, run, bytes_per_cell = _problem(ndim, dims, shape, radius, dtype, bc, kind)
+    if kind == "divkgrad":
         cands = divkgrad_candidates(dtype, quick)
-        run = lambda p, n: gs.stencil_apply_var(p, x, [k], y, n)  # noqa: E731
-        bytes_per_cell = 3
     else:
-        c = inputs.normalised_abs_weights(7, _npts(ndim, shape, radius))
-        plan = gs.stencil_plan(ndim, dims, shape, radius, "const", c, dtype, bc)
         cands = stream_candidates(ndim, shape, radius, dtype, quick)
         if ndim == 2 and steps > 1:
             cands += fused2d_candidates(radius, steps)
-        run = lambda p, n: gs.stencil_apply(p, x, y, n)  # noqa: E731
-        bytes_per_cell = 2
+        if ndim == 3 and (shape, radius) in FUSED3D_SETS:
+            steps = max(steps, 8)
+            cands += fused3d_candidates(shape, radius, dtype, quick)
     es = 4 if dtype == "f32" else 2
     cells = int(np.prod(dims))
     peak = hbm_peak()
@@ -137,13 +166,13 @@ def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=pri
         if ms is None:
             continue
         gbs = bytes_per_cell * es * cells * steps / (ms * 1e-3) / 1e9
-        ev.append({"variant": v, "ms": round(ms, 5), "alg_GBps": round(gbs, 1),
+        ev.append({"variant": v, "ms": round(ms, 5), "steps": steps, "alg_GBps": round(gbs, 1),
                    "frac_hbm": round(gbs / peak, 4)})
     ev.sort(key=lambda e: e["ms"])
     if ev:
         b = ev[0]
         log(f"  {ndim}D {shape} r{radius} {dtype} {bc} {dims} x{steps}: best {b['ms']:.4f} ms "
-            f"{b['alg_GBps']} GB/s ({b['frac_hbm']:.2%}) {b['variant']}")
+            f"{b['alg_GBps']} GB/s ({b['frac_hbm']:.2%}) {b['variant']}", flush=True)
     return (ev[0]["variant"] if ev else None), ev
 
 
@@ -157,24 +186,100 @@ def _npts(ndim, shape, r):
     return (2 * r + 1) * (2 * r * r + 2 * r + 3) // 3
 
 
-# Tuning set: (ndim, dims, shape, radius, dtype, boundary, steps, kind)
+# Tuning set: (ndim, dims, shape, radius, dtype, boundary, steps, kind).  3D keys come as
+# cubes and, for the size classes the workloads use, as z-slabs (nz * 8 <= ny, nx), whose
+# best tiles differ (few planes per tile column).
 def tuning_set(quick=False):
     s = []
     big = (512, 512, 512)
-    for shape, r in (("star", 4), ("box", 1)):
-        s.append((3, big, shape, r, "f32", "periodic", 1))
+    for bc in ("periodic", "dirichlet"):
+        for shape, r in (("star", 4), ("box", 1)):
+            s.append((3, big, shape, r, "f32", bc, 1, "const"))
     for dtype in ("f32",) if quick else ("f32", "f16", "bf16"):
         s.append((3, (384, 384, 384), "star", 1, dtype, "dirichlet", 1, "divkgrad"))
-    if not quick:
-        mid = (384, 384, 384)
-        for shape, r in (("star", 1), ("star", 2), ("box", 2), ("diamond", 2)):
-            s.append((3, mid, shape, r, "f32", "periodic", 1))
-        for dtype in ("f16", "bf16"):
-            s.append((3, mid, "star", 1, dtype, "dirichlet", 1))
-        s.append((2, (512, 512), "star", 1, "f32", "dirichlet", 10))
-        for shape, r in (("star", 1), ("star", 2), ("box", 1), ("box", 2)):
-            s.append((2, (2048, 2048), shape, r, "f32", "dirichlet", 1))
+    if quick:
+        return s
+    for dtype in ("f16", "bf16"):
+        for shape, r in (("star", 4), ("box", 1)):
+            s.append((3, big, shape, r, dtype, "periodic", 1, "const"))
+    mid = (384, 384, 384)
+    for shape, r in (("star", 1), ("star", 2), ("box", 2), ("diamond", 2)):
+        s.append((3, mid, shape, r, "f32", "periodic", 1, "const"))
+    for dtype in ("f16", "bf16"):
+        s.append((3, mid, "star", 1, dtype, "dirichlet", 1, "const"))
+    # z-slabs: a 16 M-cell slab (size class 3) and a 4 M-cell one (class 2)
+    for dims in ((32, 1024, 1024), (16, 512, 512)):
+        for shape, r in (("star", 4), ("box", 1), ("star", 1)):
+            s.append((3, dims, shape, r, "f32", "periodic", 1, "const"))
+    s.append((2, (512, 512), "star", 1, "f32", "dirichlet", 10, "const"))
+    for shape, r in (("star", 1), ("star", 2), ("box", 1), ("box", 2)):
+        s.append((2, (2048, 2048), shape, r, "f32", "dirichlet", 1, "const"))
     return s
+
+
+KERNEL_REGEX = {gs.FAMILY_STREAM: "stream_sweep", gs.FAMILY_FUSED2D: "fused2d",
+                gs.FAMILY_FUSED3D: "fused3d"}
+
+
+def replay(spec):
+    """Run one tuning key's winning variant after warm-up (the command an ncu capture
+    wraps): spec = JSON {"key": [...tuning entry...], "variant": {...}}."""
+    import torch
+    from . import build
+    build.build()
+    torch.cuda.set_device(0)
+    gs.stencil_load_dispatch_map(None)
+    d = json.loads(spec)
+    ndim, dims, shape, r, dtype, bc, steps, kind = d["key"]
+    plan, run, _ = _problem(ndim, tuple(dims), shape, r, dtype, bc, kind)
+    gs.stencil_plan_set_variant(plan, **d["variant"])
+    for _ in range(3):
+        run(plan, 1 if d["variant"]["family"] != gs.FAMILY_FUSED3D else 2)
+    torch.cuda.synchronize()
+    run(plan, 1 if d["variant"]["family"] != gs.FAMILY_FUSED3D else 2)  # the captured launch
+    torch.cuda.synchronize()
+    if gs.stencil_sync_status(plan) != 0:
+        raise SystemExit(1)
+
+
+def ncu_evidence(entry, variant, log=print):
+    """DRAM bytes and device time of one launch of the winner, from an ncu capture of a
+    single kernel (three warm-up launches are skipped); None when ncu is unavailable."""
+    import shutil
+    import subprocess
+    import sys
+    ncu = shutil.which("ncu")
+    if not ncu:
+        return None
+    spec = json.dumps({"key": list(entry), "variant": variant})
+    kern = "divkgrad" if entry[7] == "divkgrad" else KERNEL_REGEX[variant["family"]]
+    cmd = [ncu, "--metrics", "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum",
+           "--clock-control", "none", "-k", "regex:" + kern,
+           "-s", "3", "-c", "1", "--csv", sys.executable, "-m",
+           "paper_2609_06694_gb300.autotune", "--replay", spec]
+    r = subprocess.run(cmd, capture_output=True, text=True,
+                       cwd=os.path.dirname(HERE), timeout=600)
+    vals = {}
+    for line in r.stdout.splitlines():
+        cols = [c.strip('"') for c in line.split('","')]
+        if len(cols) >= 3 and cols[-3] in ("dram__bytes_read.sum", "dram__bytes_write.sum",
+                                            "gpu__time_duration.sum"):
+            unit, val = cols[-2], cols[-1].replace(",", "")
+            try:
+                x = float(val)
+            except ValueError:
+                continue
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-9,
+                     "usecond": 1e-6, "msecond": 1e-3}.get(unit, 1.0)
+            vals[cols[-3]] = x * scale
+    if len(vals) < 3:
+        log(f"    ncu gave no counters (rc {r.returncode}): {r.stdout[-300:]} {r.stderr[-300:]}")
+        return None
+    b = vals["dram__bytes_read.sum"] + vals["dram__bytes_write.sum"]
+    t = vals["gpu__time_duration.sum"]
+    return {"dram_bytes_read": vals["dram__bytes_read.sum"],
+            "dram_bytes_write": vals["dram__bytes_write.sum"], "kernel_seconds": t,
+            "dram_GBps": round(b / t / 1e9, 1), "frac_hbm_dram": round(b / t / 1e9 / hbm_peak(), 4)}
 
 
 def main():
@@ -183,36 +288,53 @@ def main():
     ap.add_argument("--out", default=DEFAULT_MAP)
     ap.add_argument("--evidence", default=DEFAULT_EVIDENCE)
     ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--no-ncu", action="store_true",
+                    help="skip the ncu capture of each winner (timings only)")
+    ap.add_argument("--replay", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.replay:
+        replay(args.replay)
+        return
     from . import build
     build.build()
     torch.cuda.set_device(0)
     gs.stencil_load_dispatch_map(None)
     lines = ["# dispatch map written by paper_2609_06694_gb300.autotune on "
              + torch.cuda.get_device_name(0),
-             "# ndim shape radius dtype boundary kind size_class : "
+             "# ndim shape radius dtype boundary kind size_class geometry : "
              "family block_x block_y vec_y z_chunk fuse tile_x tile_y stages"]
     evidence = []
+    winners = []
     for entry in tuning_set(args.quick):
-        ndim, dims, shape, r, dtype, bc, steps = entry[:7]
-        kind = entry[7] if len(entry) > 7 else "const"
+        ndim, dims, shape, r, dtype, bc, steps, kind = entry
         best, ev = tune_key(ndim, dims, shape, r, dtype, bc, steps, args.quick, kind=kind)
+        torch.cuda.empty_cache()
         if best is None:
             continue
         cls = gs.stencil_size_class(int(np.prod(dims)))
-        key = [ndim, SHAPE_ID[shape], r, DTYPE_ID[dtype], BC_ID[bc], KIND_ID[kind], cls]
+        geo = gs.stencil_geometry_class(ndim, dims)
+        key = [ndim, SHAPE_ID[shape], r, DTYPE_ID[dtype], BC_ID[bc], KIND_ID[kind], cls, geo]
         val = [best.get(k, 0) for k in ("family", "block_x", "block_y", "vec_y", "z_chunk",
                                         "fuse", "tile_x", "tile_y", "stages")]
         lines.append(" ".join(map(str, key)) + " : " + " ".join(map(str, val)))
         evidence.append({"key": {"ndim": ndim, "dims": list(dims), "shape": shape, "radius": r,
-                                 "dtype": dtype, "boundary": bc, "steps": steps, "kind": kind,
-                                 "size_class": cls},
+                                 "dtype": dtype, "boundary": bc, "steps": ev[0]["steps"],
+                                 "kind": kind, "size_class": cls, "geometry": geo},
                          "candidates_timed": len(ev), "fastest": ev[:10]})
+        winners.append((entry, best))
+    if not args.no_ncu:
+        for (entry, best), e in zip(winners, evidence):
+            e["winner_ncu"] = ncu_evidence(entry, best)
+            print(f"  ncu {entry[:6]}: {e['winner_ncu']}", flush=True)
     with open(args.out, "w") as f:
         f.write("\n".join(lines) + "\n")
     with open(args.evidence, "w") as f:
         json.dump({"device": torch.cuda.get_device_name(0), "when": time.strftime("%F %T"),
-                   "hbm_peak_GBps": hbm_peak(), "keys": evidence}, f, indent=1)
+                   "hbm_peak_GBps": hbm_peak(),
+                   "ncu": "winner_ncu: one launch of the winning variant after three warm-up "
+                          "launches, ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,"
+                          "gpu__time_duration.sum --clock-control none",
+                   "keys": evidence}, f, indent=1)
     print(f"wrote {args.out} and {args.evidence}")
 
 

@@ -52,7 +52,7 @@ std::vector<int32_t> make_offsets(int ndim, int shape, int r) {
 // Dispatch map
 // ---------------------------------------------------------------------------------------
 struct MapEntry {
-    int key[7];  // ndim shape radius dtype boundary kind size_class
+    int key[8];  // ndim shape radius dtype boundary kind size_class geometry (-1: any)
     stencil_variant v;
 };
 static std::mutex g_map_mu;
@@ -63,6 +63,13 @@ int size_class_of(int64_t cells) {
     if (cells < (int64_t)1 << 20) return 1;
     if (cells < (int64_t)1 << 24) return 2;
     return 3;
+}
+
+// Grid geometry class: 1 for a 3D slab thin in z (nz at most 1/8 of ny and of nx: few planes
+// per tile column, so the z chunks and halo planes weigh differently), 0 otherwise.
+int geometry_class_of(int ndim, const int64_t *d) {
+    if (ndim == 3 && d[0] * 8 <= d[1] && d[0] * 8 <= d[2]) return 1;
+    return 0;
 }
 
 // Built-in defaults (used when the map has no entry for a key).
@@ -111,11 +118,12 @@ static stencil_variant default_variant(const stencil_plan_s &p) {
 
 static bool lookup_map(const stencil_plan_s &p, stencil_variant *out) {
     std::lock_guard<std::mutex> lk(g_map_mu);
-    const int key[7] = {p.ndim, p.shape, p.radius, p.dtype, p.boundary, p.kind,
-                        size_class_of(p.dims[0] * p.dims[1] * p.dims[2])};
+    const int key[8] = {p.ndim, p.shape, p.radius, p.dtype, p.boundary, p.kind,
+                        size_class_of(p.dims[0] * p.dims[1] * p.dims[2]),
+                        geometry_class_of(p.ndim, p.dims)};
     for (const MapEntry &e : g_map) {
         bool ok = true;
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < 8; ++i)
             if (e.key[i] != key[i] && e.key[i] != -1) ok = false;
         if (ok) {
             *out = e.v;
@@ -395,6 +403,13 @@ uint64_t stencil_launch_count(void) { return g_launches.load(); }
 
 int stencil_size_class(int64_t cells) { return size_class_of(cells); }
 
+int stencil_geometry_class(int ndim, const int64_t *dims) {
+    if ((ndim != 2 && ndim != 3) || !dims) return STENCIL_ERR_BADARG;
+    int64_t d[3] = {1, 1, 1};
+    for (int i = 0; i < ndim; ++i) d[3 - ndim + i] = dims[i];
+    return geometry_class_of(ndim, d);
+}
+
 const char *stencil_strerror(int code) {
     switch (code) {
     case STENCIL_OK: return "ok";
@@ -652,13 +667,24 @@ int stencil_load_dispatch_map(const char *path) {
             if (hash) *hash = 0;
             MapEntry e;
             std::memset(&e, 0, sizeof(e));
-            int n = std::sscanf(line, "%d %d %d %d %d %d %d : %d %d %d %d %d %d %d %d %d",
-                                &e.key[0], &e.key[1], &e.key[2], &e.key[3], &e.key[4], &e.key[5],
-                                &e.key[6], &e.v.family, &e.v.block_x, &e.v.block_y, &e.v.vec_y,
-                                &e.v.z_chunk, &e.v.fuse, &e.v.tile_x, &e.v.tile_y, &e.v.stages);
-            if (n == 15 || n == 16) {  // the ring depth is optional (0 = automatic)
+            e.key[7] = -1;  // no geometry field: any geometry
+            char *colon = std::strchr(line, ':');
+            int nk = 0, nv = 0;
+            if (colon) {
+                *colon = 0;
+                nk = std::sscanf(line, "%d %d %d %d %d %d %d %d", &e.key[0], &e.key[1],
+                                 &e.key[2], &e.key[3], &e.key[4], &e.key[5], &e.key[6],
+                                 &e.key[7]);
+                nv = std::sscanf(colon + 1, "%d %d %d %d %d %d %d %d %d", &e.v.family,
+                                 &e.v.block_x, &e.v.block_y, &e.v.vec_y, &e.v.z_chunk,
+                                 &e.v.fuse, &e.v.tile_x, &e.v.tile_y, &e.v.stages);
+            }
+            // 7 or 8 key fields (the geometry is optional), 8 or 9 values (the ring depth is
+            // optional: 0 = automatic)
+            if ((nk == 7 || nk == 8) && (nv == 8 || nv == 9)) {
                 entries.push_back(e);
             } else {
+                if (colon) *colon = ':';
                 bool blank = true;
                 for (char *c = line; *c; ++c)
                     if (!std::isspace((unsigned char)*c)) blank = false;

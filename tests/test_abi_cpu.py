@@ -254,6 +254,26 @@ def test_size_classes():
         [0, 1, 2, 3, 3]
 
 
+def test_geometry_classes_and_slab_keys(tmp_path):
+    assert gs.stencil_geometry_class(3, (512, 512, 512)) == 0
+    assert gs.stencil_geometry_class(3, (32, 1024, 1024)) == 1
+    assert gs.stencil_geometry_class(3, (64, 512, 511)) == 0      # nz * 8 > nx
+    assert gs.stencil_geometry_class(2, (8, 4096)) == 0           # 2D grids: one class
+    # a slab-only entry, then a catch-all one for the same key without the geometry field
+    m = tmp_path / "map.txt"
+    m.write_text("3 0 4 0 1 0 3 1 : 1 32 4 2 48 1 0 0 3\n"
+                 "3 0 4 0 1 0 3 : 1 32 8 1 16 1 0 0\n")
+    gs.stencil_load_dispatch_map(str(m))
+    try:
+        c = np.ones(25)
+        slab = gs.stencil_plan(3, (32, 1024, 1024), "star", 4, "const", c, "f32", "periodic")
+        cube = gs.stencil_plan(3, (256, 256, 256), "star", 4, "const", c, "f32", "periodic")
+        assert gs.stencil_plan_get_variant(slab)["z_chunk"] == 48
+        assert gs.stencil_plan_get_variant(cube)["z_chunk"] == 16
+    finally:
+        gs.stencil_load_dispatch_map(None)
+
+
 def test_library_missing_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(api, "_LIB", None)
     monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
@@ -283,6 +303,8 @@ def test_autotuner_candidates_are_variants_the_library_accepts():
             cands = autotune.fused2d_candidates(r, steps)
         else:
             cands = autotune.stream_candidates(ndim, shape, r, dtype)
+            if ndim == 3 and (shape, r) in autotune.FUSED3D_SETS:
+                cands = cands + autotune.fused3d_candidates(shape, r, dtype)
         assert cands, key
         for v in cands:
             gs.stencil_plan_set_variant(plan, **v)
@@ -324,10 +346,16 @@ def test_committed_dispatch_map_selects_its_entries():
             if not line:
                 continue
             key, val = line.split(":")
-            ndim, shape, r, dt, bc, kind, cls = (int(t) for t in key.split())
+            fields = [int(t) for t in key.split()]
+            ndim, shape, r, dt, bc, kind, cls = fields[:7]
+            geo = fields[7] if len(fields) > 7 else 0
             want = dict(zip(names, (int(t) for t in val.split())))
-            dims = {3: (256, 256, 256), 2: (4096, 4096)}[ndim] if cls == 3 else \
-                {3: (128, 128, 128), 2: (1024, 1024)}[ndim] if cls == 2 else (512, 512)
+            if geo == 1:  # z-slabs
+                dims = (32, 1024, 1024) if cls == 3 else (16, 512, 512)
+            else:
+                dims = {3: (256, 256, 256), 2: (4096, 4096)}[ndim] if cls == 3 else \
+                    {3: (128, 128, 128), 2: (1024, 1024)}[ndim] if cls == 2 else (512, 512)
+            assert gs.stencil_geometry_class(ndim, dims) == geo, (line, dims)
             assert gs.stencil_size_class(int(np.prod(dims))) == cls, (line, dims)
             plan = _plan_for(ndim, dims, shapes[shape], r, dtypes[dt],
                              "periodic" if bc == 1 else "dirichlet", kinds[kind])
