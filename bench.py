@@ -212,7 +212,7 @@ def bench_ours(args):
     build.build()
     import paper_2609_06694_gb300 as gs
 
-    if args.only in ("divkgrad", "var", "wave", "batch"):
+    if args.only in ("divkgrad", "var", "wave", "batch", "fused3d", "reaction", "box2"):
         profile_case(args)
         return
     W = build_workload(device, args.grid)
@@ -344,7 +344,32 @@ def profile_case(args):
     import paper_2609_06694_gb300 as gs
     from paper_2609_06694_gb300 import inputs
     from paper_2609_06694_gb300 import wave as W
-    if args.only == "divkgrad":
+    if args.only in ("fused3d", "reaction", "box2"):
+        # fused3d: two fused 7-point steps per launch at 512^3 (the dispatch map's choice for
+        # this key); reaction: one Allen-Cahn step with the 7-point Laplacian at 512^3;
+        # box2: one sweep of the 125-point box at 384^3 (the compute-bound corner)
+        n = args.grid if args.grid != N else (384 if args.only == "box2" else 512)
+        dims = (n, n, n)
+        x = inputs.to_storage(inputs.uniform(2003, dims), "f32").cuda()
+        y = torch.empty_like(x)
+        if args.only == "box2":
+            c = inputs.normalised_abs_weights(7, 125)
+            plan = gs.stencil_plan(3, dims, "box", 2, "const", c, "f32", "periodic")
+            fn = lambda: gs.stencil_apply(plan, x, y, 1)  # noqa: E731
+        else:
+            c7 = np.array([1.0, 1.0, 1.0, -6.0, 1.0, 1.0, 1.0]) / 6.0
+            plan = gs.stencil_plan(3, dims, "star", 1, "const", c7, "f32", "periodic")
+            if args.only == "fused3d":
+                gs.stencil_plan_set_variant(plan, family=gs.FAMILY_FUSED3D, block_x=32,
+                                            block_y=6, vec_y=2, z_chunk=64, fuse=2, tile_x=0,
+                                            tile_y=0, stages=6)
+                fn = lambda: gs.stencil_apply(plan, x, y, 2)  # noqa: E731
+            else:
+                fn = lambda: gs.stencil_apply_reaction(plan, x, y, 1, 0.1, 1.0, -1.0)  # noqa
+        for _ in range(args.warmup + args.steps):
+            fn()
+        rc = gs.stencil_sync_status(plan)
+    elif args.only == "divkgrad":
         n = args.grid if args.grid != N else 384
         plan = gs.stencil_plan(3, (n, n, n), "star", 1, "divkgrad", None, "f32", "dirichlet")
         k = inputs.to_storage(inputs.lognormal_k(3002, (n, n, n)), "f32").cuda()
@@ -710,7 +735,8 @@ def main():
     ap.add_argument("--no-ratios", action="store_true",
                     help="skip the adjoint / batched / div(k grad u) / wave measurements that "
                          "the bench line carries under metric_ratios")
-    ap.add_argument("--only", choices=["star", "box", "divkgrad", "var", "wave", "batch"],
+    ap.add_argument("--only", choices=["star", "box", "divkgrad", "var", "wave", "batch",
+                                       "fused3d", "reaction", "box2"],
                     default=None,
                     help="profiling case: only the 1-sweep call of one stencil, no JSON line")
     ap.add_argument("--grid", type=int, default=N, help="cube side (profiling cases only)")

@@ -226,6 +226,15 @@ typedef struct {
  * `items` must outlive the batch; the items array is copied. */
 int stencil_batch_plan(stencil_batch *out, const stencil_batch_item *items, int n, int steps);
 
+/* stencil_batch_plan_tiles -- stencil_batch_plan with the launch shape chosen by the caller
+ * (the autotuner's knob): output tiles of tile_y x tile_x cells, `fuse` steps per group (a
+ * group's steps run in a tile grown by radius x fuse cells, with the intermediate levels
+ * rounded to the storage type in shared memory, so the result does not depend on fuse; one
+ * device-wide barrier per group).  0 selects the default (32 x 120 tiles, one step per
+ * group).  UNSUPPORTED when the grown tile does not fit in shared memory. */
+int stencil_batch_plan_tiles(stencil_batch *out, const stencil_batch_item *items, int n,
+                             int steps, int tile_y, int tile_x, int fuse);
+
 /* stencil_batch_launch -- launch the captured graph on `stream`. */
 int stencil_batch_launch(stencil_batch b, void *stream);
 

@@ -78,6 +78,7 @@ def _lib():
         "stencil_apply_host": ([P, P, P, I, P], I),
         "stencil_sync_status": ([P, P], I),
         "stencil_batch_plan": ([ctypes.POINTER(P), P, I, I], I),
+        "stencil_batch_plan_tiles": ([ctypes.POINTER(P), P, I, I, I, I, I], I),
         "stencil_batch_launch": ([P, P], I),
         "stencil_batch_status": ([P, P], I),
         "stencil_batch_destroy": ([P], I),
@@ -329,8 +330,9 @@ class Batch:
             self.handle = None
 
 
-def stencil_batch_plan(items, steps) -> Batch:
-    """items: sequence of (Plan, in_tensor, out_tensor); all 2D const plans."""
+def stencil_batch_plan(items, steps, tile_y=0, tile_x=0, fuse=0) -> Batch:
+    """items: sequence of (Plan, in_tensor, out_tensor); all 2D const plans.  tile_y, tile_x,
+    fuse: the launch shape (0: the library's default)."""
     lib = _lib()
     arr = (stencil_batch_item * len(items))()
     for i, (plan, inp, out) in enumerate(items):
@@ -340,7 +342,8 @@ def stencil_batch_plan(items, steps) -> Batch:
         arr[i].in_ = inp.data_ptr()
         arr[i].out = out.data_ptr()
     h = ctypes.c_void_p()
-    _check(lib.stencil_batch_plan(ctypes.byref(h), arr, len(items), int(steps)),
+    _check(lib.stencil_batch_plan_tiles(ctypes.byref(h), arr, len(items), int(steps),
+                                        int(tile_y), int(tile_x), int(fuse)),
            "stencil_batch_plan")
     return Batch(h.value, list(items))
 

@@ -269,8 +269,11 @@ def ncu_evidence(entry, variant, log=print):
                 x = float(val)
             except ValueError:
                 continue
-            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-9,
-                     "usecond": 1e-6, "msecond": 1e-3}.get(unit, 1.0)
+            scale = {"byte": 1, "B": 1, "Kbyte": 1e3, "KB": 1e3, "Mbyte": 1e6, "MB": 1e6,
+                     "Gbyte": 1e9, "GB": 1e9, "nsecond": 1e-9, "ns": 1e-9, "usecond": 1e-6,
+                     "us": 1e-6, "msecond": 1e-3, "ms": 1e-3, "second": 1.0, "s": 1.0}.get(unit)
+            if scale is None:
+                continue
             vals[cols[-3]] = x * scale
     if len(vals) < 3:
         log(f"    ncu gave no counters (rc {r.returncode}): {r.stdout[-300:]} {r.stderr[-300:]}")

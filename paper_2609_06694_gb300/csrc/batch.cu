@@ -207,15 +207,24 @@ static cudaError_t batch_enqueue(stencil_batch_s *b, cudaStream_t s) {
 extern "C" {
 
 int stencil_batch_plan(stencil_batch *out, const stencil_batch_item *items, int n, int steps) {
+    return stencil_batch_plan_tiles(out, items, n, steps, 0, 0, 0);
+}
+
+int stencil_batch_plan_tiles(stencil_batch *out, const stencil_batch_item *items, int n,
+                             int steps, int tile_y, int tile_x, int fuse) {
     if (!out) return STENCIL_ERR_BADARG;
     *out = nullptr;
     if (!items || n < 1 || steps < 1) return STENCIL_ERR_BADARG;
+    if (tile_y < 0 || tile_x < 0 || fuse < 0 || tile_y > 1024 || tile_x > 1024 || fuse > 64)
+        return STENCIL_ERR_BADARG;
     stencil_batch_s *b = new (std::nothrow) stencil_batch_s();
     if (!b) return STENCIL_ERR_OOM;
     b->n = n;
     b->steps = steps;
-    // one step per group (a barrier between steps); tiles of 32 x 120 cells
-    b->fuse = 1;
+    // defaults: one step per group (a barrier between steps), tiles of 32 x 120 cells
+    if (tile_y > 0) b->tile_y = tile_y;
+    if (tile_x > 0) b->tile_x = tile_x;
+    b->fuse = fuse > 0 ? std::min(fuse, steps) : 1;
     b->groups = (steps + b->fuse - 1) / b->fuse;
     int max_r = 1;
     std::vector<BatchGrid> grids(n);
@@ -269,6 +278,10 @@ int stencil_batch_plan(stencil_batch *out, const stencil_batch_item *items, int 
     // large grids' tiles first so that the ragged end of each step is made of small work
     b->ntiles = (int)tiles.size();
     b->smem = fused2d_smem_bytes(b->tile_x, b->tile_y, max_r, b->fuse);
+    if (b->smem > 227 * 1024) {  // the tile with its halo does not fit in shared memory
+        batch_free(b);
+        return STENCIL_ERR_UNSUPPORTED;
+    }
     if (cudaFuncSetAttribute(batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)b->smem) != cudaSuccess) {
         batch_free(b);
