@@ -293,7 +293,9 @@ int stencil_plan_set_variant(stencil_handle h, const stencil_variant *v);
  * text file at `path` (format: lines "ndim shape radius dtype boundary kind size_class
  * [geometry] : family block_x block_y vec_y z_chunk fuse tile_x tile_y [stages]", '#'
  * comments; a key field of -1 matches anything, a missing geometry field reads as -1 and a
- * missing stages field as 0; the first matching line wins).  Plans created
+ * missing stages field as 0; the first matching line wins; lines "batch dtype : tile_y
+ * tile_x fuse" give stencil_batch_plan its launch shape for batches of that storage type).
+ * Plans created
  * afterwards use it.  NULL restores the built-in defaults.  If the environment variable
  * STENCIL_DISPATCH_MAP names a file, it is loaded once before the first stencil_plan. */
 int stencil_load_dispatch_map(const char *path);

@@ -217,6 +217,66 @@ def tuning_set(quick=False):
     return s
 
 
+def batch_items(dtype):
+    """The batched workload: 256 2D grids, sides log-uniform in [64, 2048] per axis, star r1/r2
+    and box 3x3/5x5 with seeded weights, zero Dirichlet; (plan, in, out) triples."""
+    import torch
+    items = []
+    for sp in inputs.batched_grid_specs():
+        d = (sp["ny"], sp["nx"])
+        c = inputs.normalised_abs_weights(sp["weight_seed"], _npts(2, sp["shape"], sp["radius"]))
+        pl = gs.stencil_plan(2, d, sp["shape"], sp["radius"], "const", c, dtype, "dirichlet")
+        xi = inputs.to_storage(inputs.uniform(sp["input_seed"], d), dtype).cuda()
+        items.append((pl, xi, torch.empty_like(xi)))
+    return items
+
+
+def batch_candidates(quick=False):
+    """Batched launch shapes: tile height and width, steps per group (a device-wide barrier
+    per group; the grown tile recomputes its halo cells)."""
+    tys, txs, fus = ((32,), (120, 248), (1, 4)) if quick else ((16, 32, 64), (120, 248),
+                                                                (1, 2, 4, 5))
+    return [dict(tile_y=ty, tile_x=tx, fuse=f) for ty, tx, f in itertools.product(tys, txs, fus)]
+
+
+def tune_batch(dtype, steps=20, quick=False, log=print):
+    """Time every batch launch shape on the 256-grid workload; (best shape, evidence)."""
+    import torch
+    items = batch_items(dtype)
+    cells = sum(int(np.prod(x.shape)) for _, x, _ in items)
+    es = 4 if dtype == "f32" else 2
+    peak = hbm_peak()
+    ev = []
+    for cand in batch_candidates(quick):
+        try:
+            b = gs.stencil_batch_plan(items, steps, cand["tile_y"], cand["tile_x"], cand["fuse"])
+        except gs.StencilError:
+            continue
+        for _ in range(2):
+            gs.stencil_batch_launch(b)
+        ts = []
+        for _ in range(5):
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            gs.stencil_batch_launch(b)
+            e.record()
+            e.synchronize()
+            ts.append(s.elapsed_time(e))
+        if gs.stencil_batch_status(b) != 0:
+            continue
+        ms = float(np.median(ts))
+        gbs = 2 * es * cells * steps / (ms * 1e-3) / 1e9
+        ev.append({"shape": cand, "ms": round(ms, 4), "steps": steps, "alg_GBps": round(gbs, 1),
+                   "frac_hbm": round(gbs / peak, 4), "batch": gs.stencil_batch_info(b)})
+        del b
+    ev.sort(key=lambda e: e["ms"])
+    if ev:
+        log(f"  batch 256 grids {dtype} x{steps}: best {ev[0]['ms']:.3f} ms "
+            f"({ev[0]['frac_hbm']:.2%}) {ev[0]['shape']}", flush=True)
+    return (ev[0]["shape"] if ev else None), ev
+
+
 KERNEL_REGEX = {gs.FAMILY_STREAM: "stream_sweep", gs.FAMILY_FUSED2D: "fused2d",
                 gs.FAMILY_FUSED3D: "fused3d"}
 
@@ -230,6 +290,15 @@ def replay(spec):
     torch.cuda.set_device(0)
     gs.stencil_load_dispatch_map(None)
     d = json.loads(spec)
+    if "batch" in d:
+        items = batch_items(d["batch"])
+        b = gs.stencil_batch_plan(items, 20, d["shape"]["tile_y"], d["shape"]["tile_x"],
+                                  d["shape"]["fuse"])
+        for _ in range(4):  # three warm-up launches, then the captured one
+            gs.stencil_batch_launch(b)
+        if gs.stencil_batch_status(b) != 0:
+            raise SystemExit(1)
+        return
     ndim, dims, shape, r, dtype, bc, steps, kind = d["key"]
     plan, run, _ = _problem(ndim, tuple(dims), shape, r, dtype, bc, kind)
     gs.stencil_plan_set_variant(plan, **d["variant"])
@@ -251,8 +320,12 @@ def ncu_evidence(entry, variant, log=print):
     ncu = shutil.which("ncu")
     if not ncu:
         return None
-    spec = json.dumps({"key": list(entry), "variant": variant})
-    kern = "divkgrad" if entry[7] == "divkgrad" else KERNEL_REGEX[variant["family"]]
+    if entry[0] == "batch":
+        spec = json.dumps({"batch": entry[1], "shape": variant})
+        kern = "batch_persistent"
+    else:
+        spec = json.dumps({"key": list(entry), "variant": variant})
+        kern = "divkgrad" if entry[7] == "divkgrad" else KERNEL_REGEX[variant["family"]]
     cmd = [ncu, "--metrics", "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum",
            "--clock-control", "none", "-k", "regex:" + kern,
            "-s", "3", "-c", "1", "--csv", sys.executable, "-m",
@@ -325,6 +398,15 @@ def main():
                                  "kind": kind, "size_class": cls, "geometry": geo},
                          "candidates_timed": len(ev), "fastest": ev[:10]})
         winners.append((entry, best))
+    for dtype in ("f32", "bf16"):
+        best, ev = tune_batch(dtype, quick=args.quick)
+        torch.cuda.empty_cache()
+        if best is None:
+            continue
+        lines.append(f"batch {DTYPE_ID[dtype]} : {best['tile_y']} {best['tile_x']} {best['fuse']}")
+        evidence.append({"key": {"batch": dtype, "grids": 256, "steps": 20},
+                         "candidates_timed": len(ev), "fastest": ev[:10]})
+        winners.append((("batch", dtype), best))
     if not args.no_ncu:
         for (entry, best), e in zip(winners, evidence):
             e["winner_ncu"] = ncu_evidence(entry, best)

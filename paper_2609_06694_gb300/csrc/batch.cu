@@ -207,7 +207,16 @@ static cudaError_t batch_enqueue(stencil_batch_s *b, cudaStream_t s) {
 extern "C" {
 
 int stencil_batch_plan(stencil_batch *out, const stencil_batch_item *items, int n, int steps) {
-    return stencil_batch_plan_tiles(out, items, n, steps, 0, 0, 0);
+    // the dispatch map's shape for the batch's storage type, when every grid has the same one
+    BatchShape bs;
+    if (items && n > 0 && items[0].plan) {
+        const int dt = items[0].plan->dtype;
+        bool same = true;
+        for (int i = 1; i < n; ++i)
+            if (!items[i].plan || items[i].plan->dtype != dt) same = false;
+        if (same) bs = batch_shape_for(dt);
+    }
+    return stencil_batch_plan_tiles(out, items, n, steps, bs.tile_y, bs.tile_x, bs.fuse);
 }
 
 int stencil_batch_plan_tiles(stencil_batch *out, const stencil_batch_item *items, int n,

@@ -57,6 +57,12 @@ struct MapEntry {
 };
 static std::mutex g_map_mu;
 static std::vector<MapEntry> g_map;
+static BatchShape g_batch_map[3];  // per storage type; zeros: no entry
+
+BatchShape batch_shape_for(int dtype) {
+    std::lock_guard<std::mutex> lk(g_map_mu);
+    return (dtype >= 0 && dtype < 3) ? g_batch_map[dtype] : BatchShape{};
+}
 
 int size_class_of(int64_t cells) {
     if (cells < (int64_t)1 << 16) return 0;
@@ -658,6 +664,7 @@ int stencil_plan_set_variant(stencil_handle h, const stencil_variant *v) {
 
 int stencil_load_dispatch_map(const char *path) {
     std::vector<MapEntry> entries;
+    BatchShape batch[3];
     if (path) {
         FILE *f = std::fopen(path, "r");
         if (!f) return STENCIL_ERR_BADARG;
@@ -665,6 +672,18 @@ int stencil_load_dispatch_map(const char *path) {
         while (std::fgets(line, sizeof(line), f)) {
             char *hash = std::strchr(line, '#');
             if (hash) *hash = 0;
+            // "batch dtype : tile_y tile_x fuse" -- the batched launch's shape per storage type
+            int bdt = -1;
+            BatchShape bs;
+            if (std::sscanf(line, " batch %d : %d %d %d", &bdt, &bs.tile_y, &bs.tile_x,
+                            &bs.fuse) == 4) {
+                if (bdt < 0 || bdt > 2 || bs.tile_y < 1 || bs.tile_x < 1 || bs.fuse < 1) {
+                    std::fclose(f);
+                    return STENCIL_ERR_BADARG;
+                }
+                batch[bdt] = bs;
+                continue;
+            }
             MapEntry e;
             std::memset(&e, 0, sizeof(e));
             e.key[7] = -1;  // no geometry field: any geometry
@@ -698,6 +717,7 @@ int stencil_load_dispatch_map(const char *path) {
     }
     std::lock_guard<std::mutex> lk(g_map_mu);
     g_map.swap(entries);
+    for (int i = 0; i < 3; ++i) g_batch_map[i] = batch[i];
     return STENCIL_OK;
 }
 

@@ -49,5 +49,11 @@ bool overlaps(const void *a, const void *b, size_t n);
 int launch_group_with(stencil_plan_s &p, const float *cf, const void *src, void *dst, int k,
                       cudaStream_t s);
 int plan_steps_per_launch(const stencil_plan_s &p);  // steps one launch of the plan fuses
+// The batched launch's tile shape and steps per group for a storage type, from the dispatch
+// map's "batch" lines (all zero: no entry).
+struct BatchShape {
+    int tile_y = 0, tile_x = 0, fuse = 0;
+};
+BatchShape batch_shape_for(int dtype);
 int map_launch_rc(int rc);
 }  // namespace gst

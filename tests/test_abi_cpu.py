@@ -254,6 +254,18 @@ def test_size_classes():
         [0, 1, 2, 3, 3]
 
 
+def test_batch_lines_in_the_dispatch_map(tmp_path):
+    ok = tmp_path / "ok.txt"
+    ok.write_text("batch 0 : 32 248 4\nbatch 2 : 16 120 2\n3 0 4 0 1 0 3 : 1 32 8 1 16 1 0 0\n")
+    gs.stencil_load_dispatch_map(str(ok))
+    gs.stencil_load_dispatch_map(None)
+    for bad in ("batch 3 : 32 248 4\n", "batch 0 : 0 248 4\n", "batch 0 : 32 248\n"):
+        m = tmp_path / "bad.txt"
+        m.write_text(bad)
+        with pytest.raises(gs.StencilError):
+            gs.stencil_load_dispatch_map(str(m))
+
+
 def test_geometry_classes_and_slab_keys(tmp_path):
     assert gs.stencil_geometry_class(3, (512, 512, 512)) == 0
     assert gs.stencil_geometry_class(3, (32, 1024, 1024)) == 1
@@ -346,6 +358,8 @@ def test_committed_dispatch_map_selects_its_entries():
             if not line:
                 continue
             key, val = line.split(":")
+            if key.split()[0] == "batch":
+                continue  # the batched launch's shape (read by stencil_batch_plan)
             fields = [int(t) for t in key.split()]
             ndim, shape, r, dt, bc, kind, cls = fields[:7]
             geo = fields[7] if len(fields) > 7 else 0
