@@ -234,8 +234,8 @@ def batch_items(dtype):
 def batch_candidates(quick=False):
     """Batched launch shapes: tile height and width, steps per group (a device-wide barrier
     per group; the grown tile recomputes its halo cells)."""
-    tys, txs, fus = ((32,), (120, 248), (1, 4)) if quick else ((16, 32, 64), (120, 248),
-                                                                (1, 2, 4, 5))
+    tys, txs, fus = ((16, 32), (120,), (1, 2)) if quick else ((8, 16, 32, 64), (56, 120, 248),
+                                                              (1, 2, 3, 5))
     return [dict(tile_y=ty, tile_x=tx, fuse=f) for ty, tx, f in itertools.product(tys, txs, fus)]
 
 
@@ -326,10 +326,16 @@ def ncu_evidence(entry, variant, log=print):
     else:
         spec = json.dumps({"key": list(entry), "variant": variant})
         kern = "divkgrad" if entry[7] == "divkgrad" else KERNEL_REGEX[variant["family"]]
+    replay_cmd = [sys.executable, "-m", "paper_2609_06694_gb300.autotune", "--replay", spec]
+    # the same command runs to completion without ncu before it is captured
+    plain = subprocess.run(replay_cmd, capture_output=True, text=True,
+                           cwd=os.path.dirname(HERE), timeout=600)
+    if plain.returncode != 0:
+        log(f"    replay failed without ncu (rc {plain.returncode}): {plain.stderr[-300:]}")
+        return None
     cmd = [ncu, "--metrics", "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum",
            "--clock-control", "none", "-k", "regex:" + kern,
-           "-s", "3", "-c", "1", "--csv", sys.executable, "-m",
-           "paper_2609_06694_gb300.autotune", "--replay", spec]
+           "-s", "3", "-c", "1", "--csv"] + replay_cmd
     r = subprocess.run(cmd, capture_output=True, text=True,
                        cwd=os.path.dirname(HERE), timeout=600)
     vals = {}
@@ -366,6 +372,9 @@ def main():
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--no-ncu", action="store_true",
                     help="skip the ncu capture of each winner (timings only)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="retune only the batched launch shapes; keep the map's other lines "
+                         "and their evidence")
     ap.add_argument("--replay", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.replay:
@@ -381,7 +390,14 @@ def main():
              "family block_x block_y vec_y z_chunk fuse tile_x tile_y stages"]
     evidence = []
     winners = []
-    for entry in tuning_set(args.quick):
+    kept = []  # --batch-only: the previous map's per-key lines and evidence
+    if args.batch_only:
+        with open(args.out) as f:
+            lines += [ln.rstrip("\n") for ln in f
+                      if ln.strip() and not ln.startswith("#") and not ln.startswith("batch")]
+        with open(args.evidence) as f:
+            kept = [k for k in json.load(f)["keys"] if "batch" not in k["key"]]
+    for entry in ([] if args.batch_only else tuning_set(args.quick)):
         ndim, dims, shape, r, dtype, bc, steps, kind = entry
         best, ev = tune_key(ndim, dims, shape, r, dtype, bc, steps, args.quick, kind=kind)
         torch.cuda.empty_cache()
@@ -413,6 +429,7 @@ def main():
             print(f"  ncu {entry[:6]}: {e['winner_ncu']}", flush=True)
     with open(args.out, "w") as f:
         f.write("\n".join(lines) + "\n")
+    evidence = kept + evidence
     with open(args.evidence, "w") as f:
         json.dump({"device": torch.cuda.get_device_name(0), "when": time.strftime("%F %T"),
                    "hbm_peak_GBps": hbm_peak(),

@@ -189,6 +189,7 @@ def test_apply_argument_validation_needs_no_device():
     assert lib.stencil_apply_host(p.handle, None, other, 1, None) == -1
     pv = gs.stencil_plan(3, (8, 8, 8), "star", 1, "var", None, "f32", "dirichlet")
     assert lib.stencil_apply(pv.handle, buf, other, 1, None) == -1    # wrong entry for kind
+    assert lib.stencil_batch_info(None, None, None, None) == -1
 
 
 def test_variant_get_set_and_validation():

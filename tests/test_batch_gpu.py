@@ -23,7 +23,7 @@ def _dev():
     torch.cuda.set_device(0)
 
 
-def make_batch(specs, steps):
+def make_batch(specs, steps, tiles=(0, 0, 0)):
     grids = []
     for i, (ny, nx, shape, r, dtype, bc) in enumerate(specs):
         offs = oracle.offsets(2, shape, r)
@@ -34,7 +34,7 @@ def make_batch(specs, steps):
         yd = torch.empty_like(xd)
         grids.append(dict(plan=plan, offs=offs, c=c, x=x, x64=x64, xd=xd, yd=yd, dtype=dtype,
                           bc=bc))
-    batch = gs.stencil_batch_plan([(g["plan"], g["xd"], g["yd"]) for g in grids], steps)
+    batch = gs.stencil_batch_plan([(g["plan"], g["xd"], g["yd"]) for g in grids], steps, *tiles)
     return batch, grids
 
 
@@ -71,6 +71,28 @@ def test_batch_equals_plain_per_grid_bitwise():
         gs.stencil_apply(g["plan"], g["xd"], ref, steps)
         torch.cuda.synchronize()
         assert torch.equal(ref, g["yd"])
+
+
+# (tile_y, tile_x, steps per group): ragged tiles, tiles larger than small grids, deep groups
+TILINGS = [(16, 120, 1), (16, 120, 3), (8, 56, 3), (4, 8, 5), (32, 120, 2), (64, 248, 1)]
+
+
+@pytest.mark.parametrize("tiles", TILINGS)
+def test_launch_shapes_equal_plain_sweeps(tiles):
+    """Every launch shape gives the bits of plain per-grid sweeps, over ragged tiles, grids
+    smaller than one tile and periodic halos that wrap more than once."""
+    steps = 5
+    batch, grids = make_batch(MIXED, steps, tiles)
+    gs.stencil_batch_launch(batch)
+    assert gs.stencil_batch_status(batch) == 0
+    for g in grids:
+        ref = torch.empty_like(g["yd"])
+        gs.stencil_apply(g["plan"], g["xd"], ref, steps)
+        torch.cuda.synchronize()
+        assert torch.equal(ref, g["yd"]), (tiles, g["x64"].shape, g["dtype"], g["bc"])
+    g = grids[1]  # one grid against the oracle as well
+    pure, emu = oracle_run(g["x64"], g["offs"], g["c"], g["bc"], steps, g["dtype"])
+    check_steps(inputs.stored_values(g["yd"]), pure, emu, g["dtype"], f"batch tiles {tiles}")
 
 
 def test_batch_rejects_unsupported_and_bad_items():
@@ -119,9 +141,10 @@ def test_full_batch_256_grids_20_steps(dtype):
           f"FP64, {worst_emu:.2e} vs per-step rounding")
 
 
-def test_barrier_timeout_is_reported_and_context_survives():
+@pytest.mark.parametrize("tiles", [(0, 0, 0), (16, 120, 3)])
+def test_barrier_timeout_is_reported_and_context_survives(tiles):
     specs = [(64, 128, "star", 1, "f32", "dirichlet"), (50, 70, "box", 1, "f32", "periodic")]
-    batch, grids = make_batch(specs, 3)
+    batch, grids = make_batch(specs, 3, tiles)
     gs.stencil_batch_set_wait_limit(batch, 0.05, phantom_arrivals=1)
     gs.stencil_batch_launch(batch)
     assert gs.stencil_batch_status(batch) == -5  # STENCIL_ERR_TIMEOUT
