@@ -282,6 +282,15 @@ typedef struct {
                                     must be 2, vec_y 2 (f32) or 1 (16-bit storage), block_y
                                     >= 2 * radius; an odd last step runs on the streaming
                                     kernel                                                     */
+#define STENCIL_FAMILY_TENSOR 4  /* the radius-2 box (2D and 3D) on the tensor cores, Toeplitz
+                                    packing of the x direction (Sec. 6, tensor-core mapping):
+                                    f16/bf16 storage, zero Dirichlet, rows a multiple of 8
+                                    cells; tile_x = 16, 32 or 64 outputs per CTA, z_chunk
+                                    planes per CTA (0 = one wave), stages 5..12 plane slots
+                                    (0 = automatic); other fields are ignored. Accumulates in
+                                    FP32 with the coefficients split into two 16-bit parts, so
+                                    results equal the FP32 path to within rounding, not bit
+                                    for bit */
 
 /* stencil_plan_get_variant / stencil_plan_set_variant -- read or override the kernel variant
  * a plan uses (the autotuner's knob).  set validates the variant against the plan and returns

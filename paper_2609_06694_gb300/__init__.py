@@ -9,6 +9,7 @@ from .api import (  # noqa: F401
     FAMILY_FUSED2D,
     FAMILY_FUSED3D,
     FAMILY_STREAM,
+    FAMILY_TENSOR,
     Batch,
     Plan,
     StencilError,

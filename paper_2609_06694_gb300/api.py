@@ -21,6 +21,7 @@ KINDS = {"const": 0, "var": 1, "divkgrad": 2}
 FAMILY_STREAM = 1
 FAMILY_FUSED2D = 2
 FAMILY_FUSED3D = 3
+FAMILY_TENSOR = 4
 
 _ERRORS = {-1: "BADARG", -2: "UNSUPPORTED", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "BOUNDS"}
 

@@ -176,6 +176,17 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
         if (v.stages != 0 && (v.stages < 2 || v.stages > 16)) return STENCIL_ERR_BADARG;
         return STENCIL_OK;
     }
+    if (v.family == STENCIL_FAMILY_TENSOR) {
+        // the radius-2 box on the tensor cores: 16-bit storage, zero Dirichlet, rows a
+        // multiple of 8 cells; tile_x = 16, 32 or 64 outputs per CTA, 5..12 plane slots
+        if (!toeplitz_compiled(p.ndim, p.shape, p.radius, p.dtype) ||
+            p.boundary != STENCIL_DIRICHLET0 || p.dims[2] % 8 != 0)
+            return STENCIL_ERR_UNSUPPORTED;
+        if ((v.tile_x != 16 && v.tile_x != 32 && v.tile_x != 64) || v.fuse != 1 ||
+            v.z_chunk < 0 || (v.stages != 0 && (v.stages < 5 || v.stages > 12)))
+            return STENCIL_ERR_BADARG;
+        return STENCIL_OK;
+    }
     if (v.family == STENCIL_FAMILY_FUSED2D) {
         if (p.ndim != 2) return STENCIL_ERR_UNSUPPORTED;
         if (v.fuse < 1 || v.tile_x < 1 || v.tile_y < 1) return STENCIL_ERR_BADARG;
@@ -266,6 +277,7 @@ static int launch_group(stencil_plan_s &p, const float *cf, const void *src, voi
     // streaming kernel with the same tile
     if (v.family == STENCIL_FAMILY_FUSED3D && k == 2 && !slab)
         return map_launch_rc(launch_fused3d(L));
+    if (v.family == STENCIL_FAMILY_TENSOR) return map_launch_rc(launch_toeplitz(L, v.tile_x / 16));
     return map_launch_rc(launch_stream(L));
 }
 

@@ -403,3 +403,33 @@ def test_fused3d_variant_validation():
     p2 = gs.stencil_plan(2, (64, 64), "box", 1, "const", np.ones(9), "f32", "periodic")
     with pytest.raises(gs.StencilError):
         gs.stencil_plan_set_variant(p2, **f32)
+
+
+def test_tensor_variant_validation():
+    # the tensor-core family runs the radius-2 box on 16-bit storage, zero Dirichlet, rows a
+    # multiple of 8 cells; everything else is refused before any launch
+    c125 = np.ones(125) / 125
+    p = gs.stencil_plan(3, (8, 16, 16), "box", 2, "const", c125, "bf16", "dirichlet")
+    gs.stencil_plan_set_variant(p, family=gs.FAMILY_TENSOR, tile_x=32, z_chunk=0, stages=0,
+                                fuse=1)
+    assert gs.stencil_plan_get_variant(p)["family"] == gs.FAMILY_TENSOR
+    p2 = gs.stencil_plan(2, (40, 24), "box", 2, "const", np.ones(25), "f16", "dirichlet")
+    gs.stencil_plan_set_variant(p2, family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0, stages=0,
+                                fuse=1)
+    for dtype, bc, dims, shape, r, n in (("f32", "dirichlet", (8, 16, 16), "box", 2, 125),
+                                         ("bf16", "periodic", (8, 16, 16), "box", 2, 125),
+                                         ("bf16", "dirichlet", (8, 16, 20), "box", 2, 125),
+                                         ("bf16", "dirichlet", (8, 16, 16), "box", 1, 27),
+                                         ("bf16", "dirichlet", (8, 16, 16), "star", 2, 13)):
+        q = gs.stencil_plan(3, dims, shape, r, "const", np.ones(n), dtype, bc)
+        with pytest.raises(gs.StencilError) as e:
+            gs.stencil_plan_set_variant(q, family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0,
+                                        stages=0, fuse=1)
+        assert e.value.code == -2
+    for bad in (dict(tile_x=48), dict(tile_x=16, stages=4), dict(tile_x=16, stages=13),
+                dict(tile_x=16, fuse=2), dict(tile_x=16, z_chunk=-1)):
+        kw = dict(family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0, stages=0, fuse=1)
+        kw.update(bad)
+        with pytest.raises(gs.StencilError) as e:
+            gs.stencil_plan_set_variant(p, **kw)
+        assert e.value.code == -1
