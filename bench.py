@@ -212,7 +212,7 @@ def bench_ours(args):
     build.build()
     import paper_2609_06694_gb300 as gs
 
-    if args.only in ("divkgrad", "var", "wave", "batch", "fused3d", "reaction", "box2"):
+    if args.only in ("divkgrad", "var", "wave", "batch", "fused3d", "reaction", "box2", "tensor"):
         profile_case(args)
         return
     W = build_workload(device, args.grid)
@@ -337,6 +337,27 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def tuned_cuda_core_variant(ndim, dims, shape, radius, dtype, bc):
+    """The fastest non-tensor-core variant the autotuner timed for this workload, from the
+    package's dispatch evidence (None if the key is not there)."""
+    import paper_2609_06694_gb300 as gs
+    path = os.path.join(os.path.dirname(gs.api.DISPATCH_MAP), "dispatch_evidence.json")
+    try:
+        with open(path) as f:
+            keys = json.load(f)["keys"]
+    except (OSError, ValueError, KeyError):
+        return None
+    for k in keys:
+        kk = k["key"]
+        if (kk.get("ndim") == ndim and tuple(kk.get("dims", ())) == tuple(dims) and
+                kk.get("shape") == shape and kk.get("radius") == radius and
+                kk.get("dtype") == dtype and kk.get("boundary") == bc):
+            for e in k["fastest"]:
+                if e["variant"]["family"] != gs.FAMILY_TENSOR:
+                    return e["variant"]
+    return None
+
+
 def profile_case(args):
     """Single-kernel profiling cases of the other workloads (no JSON benchmark line)."""
     import torch
@@ -344,7 +365,21 @@ def profile_case(args):
     import paper_2609_06694_gb300 as gs
     from paper_2609_06694_gb300 import inputs
     from paper_2609_06694_gb300 import wave as W
-    if args.only in ("fused3d", "reaction", "box2"):
+    if args.only == "tensor":
+        # the 125-point box at 384^3 in bf16, zero Dirichlet, on the tensor cores (Toeplitz
+        # packing, 64 outputs per CTA along x, one wave of z chunks)
+        n = args.grid if args.grid != N else 384
+        dims = (n, n, n)
+        c, _ = inputs.normalised_sum_weights(2002, 125)
+        x = inputs.to_storage(inputs.uniform(2003, dims), "bf16").cuda()
+        y = torch.empty_like(x)
+        plan = gs.stencil_plan(3, dims, "box", 2, "const", c, "bf16", "dirichlet")
+        gs.stencil_plan_set_variant(plan, family=gs.FAMILY_TENSOR, block_y=1, tile_x=64,
+                                    z_chunk=0, stages=0, fuse=1)
+        for _ in range(args.warmup + args.steps):
+            gs.stencil_apply(plan, x, y, 1)
+        rc = gs.stencil_sync_status(plan)
+    elif args.only in ("fused3d", "reaction", "box2"):
         # fused3d: two fused 7-point steps per launch at 512^3 (the dispatch map's choice for
         # this key); reaction: one Allen-Cahn step with the 7-point Laplacian at 512^3;
         # box2: one sweep of the 125-point box at 384^3 (the compute-bound corner)
@@ -590,6 +625,43 @@ def measure_metric_ratios(W3=None, wave=True):
         del W3
         torch.cuda.empty_cache()
 
+    # the 125-point box in 16-bit storage: the CUDA-core streaming sweep against the tensor-core
+    # Toeplitz kernel (the dispatch map's variant for the key when it picks the tensor family,
+    # else 64 outputs per CTA and one wave of z chunks)
+    n = 384
+    c125, _ = inputs.normalised_sum_weights(2002, 125)
+    for dt in ("bf16", "f16"):
+        dims = (n, n, n)
+        x = inputs.to_storage(inputs.uniform(2003, dims), dt).cuda()
+        y = torch.empty_like(x)
+        core = gs.stencil_plan(3, dims, "box", 2, "const", c125, dt, "dirichlet")
+        tens = gs.stencil_plan(3, dims, "box", 2, "const", c125, dt, "dirichlet")
+        if gs.stencil_plan_get_variant(tens)["family"] != gs.FAMILY_TENSOR:
+            gs.stencil_plan_set_variant(tens, family=gs.FAMILY_TENSOR, block_y=1, tile_x=64,
+                                        z_chunk=0, stages=0, fuse=1)
+        # the CUDA-core side runs the fastest CUDA-core variant the autotuner timed for this
+        # key (its evidence file), else the library default
+        best = tuned_cuda_core_variant(3, dims, "box", 2, dt, "dirichlet")
+        if best is not None:
+            gs.stencil_plan_set_variant(core, **best)
+        elif gs.stencil_plan_get_variant(core)["family"] == gs.FAMILY_TENSOR:
+            gs.stencil_plan_set_variant(core, family=gs.FAMILY_STREAM, block_x=16, block_y=8,
+                                        vec_y=2, z_chunk=64, fuse=1, tile_x=0, tile_y=0,
+                                        stages=0)
+        ms_c = _time(lambda: gs.stencil_apply(core, x, y, 1))
+        ms_t = _time(lambda: gs.stencil_apply(tens, x, y, 1))
+        useful = 2 * 125 * n ** 3  # FLOPs of the 125-point sweep
+        out[f"box2_384_{dt}_tensor_cores"] = {
+            "workload": f"384^3 {dt} zero-Dirichlet 125-point box, 1 sweep: tensor cores "
+                        "(Toeplitz packing, tcgen05) vs the CUDA-core streaming sweep",
+            "ms_cuda_cores": round(ms_c, 4), "ms_tensor_cores": round(ms_t, 4),
+            "tensor_speedup": round(ms_c / ms_t, 3),
+            "useful_TFLOPs_tensor": round(useful / ms_t / 1e9, 1),
+            "tensor_variant": gs.stencil_plan_get_variant(tens),
+            "cuda_core_variant": gs.stencil_plan_get_variant(core),
+            "frac_hbm_tensor": _frac(4 * n ** 3 / 1e9, ms_t, peak)[1]}
+        del core, tens, x, y
+
     n = 384
     for dt in ("f32", "bf16"):
         es = 4 if dt == "f32" else 2
@@ -735,7 +807,7 @@ def main():
     ap.add_argument("--no-ratios", action="store_true",
                     help="skip the adjoint / batched / div(k grad u) / wave measurements that "
                          "the bench line carries under metric_ratios")
-    ap.add_argument("--only", choices=["star", "box", "divkgrad", "var", "wave", "batch",
+    ap.add_argument("--only", choices=["star", "box", "divkgrad", "var", "wave", "batch", "tensor",
                                        "fused3d", "reaction", "box2"],
                     default=None,
                     help="profiling case: only the 1-sweep call of one stencil, no JSON line")

@@ -286,8 +286,12 @@ typedef struct {
                                     packing of the x direction (Sec. 6, tensor-core mapping):
                                     f16/bf16 storage, zero Dirichlet, rows a multiple of 8
                                     cells; tile_x = 16, 32 or 64 outputs per CTA, z_chunk
-                                    planes per CTA (0 = one wave), stages 5..12 plane slots
-                                    (0 = automatic); other fields are ignored. Accumulates in
+                                    planes per CTA (0 = one wave), stages plane slots (0 =
+                                    automatic, else 5..12), block_y = 2 stages each plane's
+                                    A operand once in tensor memory (tile_x 16, stages 2..12)
+                                    instead of reading it from shared memory in every MMA
+                                    (block_y 0 or 1; other values are refused); block_x and
+                                    vec_y are ignored. Accumulates in
                                     FP32 with the coefficients split into two 16-bit parts, so
                                     results equal the FP32 path to within rounding, not bit
                                     for bit */

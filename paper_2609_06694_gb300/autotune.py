@@ -111,6 +111,23 @@ def divkgrad_candidates(dtype, quick=False):
     return out
 
 
+def tensor_candidates(ndim, quick=False):
+    """Tensor-core (Toeplitz) variants of the radius-2 box: 16, 32 or 64 outputs per CTA
+    along x, A read from shared memory by every MMA (block_y 1) or, for 16-wide tiles, staged
+    in tensor memory once per plane (block_y 2); z chunk (0 = one wave) and ring depth."""
+    out = []
+    zcs = (0,) if ndim == 2 else ((0, 32) if quick else (0, 16, 32, 48, 64))
+    for (tx, by), zc in itertools.product(((16, 1), (32, 1), (64, 1), (16, 2)), zcs):
+        out.append(dict(family=gs.FAMILY_TENSOR, block_x=0, block_y=by, vec_y=0, z_chunk=zc,
+                        fuse=1, tile_x=tx, tile_y=0, stages=0))
+    return out
+
+
+def tensor_applies(ndim, dims, shape, radius, dtype, bc, kind):
+    return (kind == "const" and shape == "box" and radius == 2 and dtype != "f32" and
+            bc == "dirichlet" and dims[-1] % 8 == 0)
+
+
 def fused3d_candidates(shape, radius, dtype, quick=False):
     """Two-step fused 3D variants (temporal blocking): rows of threads, z chunk, ring depth."""
     bx = 32 if dtype == "f32" else 16
@@ -157,6 +174,8 @@ def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=pri
         if ndim == 3 and (shape, radius) in FUSED3D_SETS:
             steps = max(steps, 8)
             cands += fused3d_candidates(shape, radius, dtype, quick)
+        if tensor_applies(ndim, dims, shape, radius, dtype, bc, kind):
+            cands += tensor_candidates(ndim, quick)
     es = 4 if dtype == "f32" else 2
     cells = int(np.prod(dims))
     peak = hbm_peak()
@@ -207,6 +226,9 @@ def tuning_set(quick=False):
         s.append((3, mid, shape, r, "f32", "periodic", 1, "const"))
     for dtype in ("f16", "bf16"):
         s.append((3, mid, "star", 1, dtype, "dirichlet", 1, "const"))
+        # the 125-point box in 16-bit storage: CUDA cores against the tensor cores
+        s.append((3, mid, "box", 2, dtype, "dirichlet", 1, "const"))
+        s.append((2, (2048, 2048), "box", 2, dtype, "dirichlet", 1, "const"))
     # z-slabs: a 16 M-cell slab (size class 3) and a 4 M-cell one (class 2)
     for dims in ((32, 1024, 1024), (16, 512, 512)):
         for shape, r in (("star", 4), ("box", 1), ("star", 1)):
@@ -278,7 +300,7 @@ def tune_batch(dtype, steps=20, quick=False, log=print):
 
 
 KERNEL_REGEX = {gs.FAMILY_STREAM: "stream_sweep", gs.FAMILY_FUSED2D: "fused2d",
-                gs.FAMILY_FUSED3D: "fused3d"}
+                gs.FAMILY_FUSED3D: "fused3d", gs.FAMILY_TENSOR: "toeplitz"}
 
 
 def replay(spec):
@@ -364,6 +386,26 @@ def ncu_evidence(entry, variant, log=print):
             "dram_GBps": round(b / t / 1e9, 1), "frac_hbm_dram": round(b / t / 1e9 / hbm_peak(), 4)}
 
 
+def describe(entry):
+    """Human-readable text of a tuning entry, matched by --keys."""
+    ndim, dims, shape, r, dtype, bc, steps, kind = entry
+    return f"{ndim}D {shape} r{r} {dtype} {bc} {kind} {'x'.join(map(str, dims))}"
+
+
+def key_text(entry):
+    """The dispatch-map key of a tuning entry as written in the map."""
+    ndim, dims, shape, r, dtype, bc, steps, kind = entry
+    cls = gs.stencil_size_class(int(np.prod(dims)))
+    geo = gs.stencil_geometry_class(ndim, dims)
+    return " ".join(map(str, [ndim, SHAPE_ID[shape], r, DTYPE_ID[dtype], BC_ID[bc],
+                              KIND_ID[kind], cls, geo]))
+
+
+def evidence_key_text(k):
+    return key_text((k["ndim"], tuple(k["dims"]), k["shape"], k["radius"], k["dtype"],
+                     k["boundary"], k["steps"], k["kind"]))
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -372,6 +414,9 @@ def main():
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--no-ncu", action="store_true",
                     help="skip the ncu capture of each winner (timings only)")
+    ap.add_argument("--keys", default=None,
+                    help="retune only the keys whose description contains this text (e.g. "
+                         "'box r2'); keep the map's other lines and their evidence")
     ap.add_argument("--batch-only", action="store_true",
                     help="retune only the batched launch shapes; keep the map's other lines "
                          "and their evidence")
@@ -390,14 +435,24 @@ def main():
              "family block_x block_y vec_y z_chunk fuse tile_x tile_y stages"]
     evidence = []
     winners = []
-    kept = []  # --batch-only: the previous map's per-key lines and evidence
-    if args.batch_only:
+    kept = []  # --batch-only / --keys: the previous map's other lines and evidence
+    entries = [] if args.batch_only else tuning_set(args.quick)
+    if args.keys:
+        entries = [e for e in entries if args.keys in describe(e)]
+    if args.batch_only or args.keys:
+        retuned = {key_text(e) for e in entries}
         with open(args.out) as f:
-            lines += [ln.rstrip("\n") for ln in f
-                      if ln.strip() and not ln.startswith("#") and not ln.startswith("batch")]
+            old_lines = [ln.rstrip("\n") for ln in f if ln.strip() and not ln.startswith("#")]
         with open(args.evidence) as f:
-            kept = [k for k in json.load(f)["keys"] if "batch" not in k["key"]]
-    for entry in ([] if args.batch_only else tuning_set(args.quick)):
+            old_ev = json.load(f)["keys"]
+        if args.batch_only:
+            lines += [ln for ln in old_lines if not ln.startswith("batch")]
+            kept = [k for k in old_ev if "batch" not in k["key"]]
+        else:
+            lines += [ln for ln in old_lines if ln.split(":")[0].strip() not in retuned]
+            kept = [k for k in old_ev if "batch" in k["key"] or
+                    evidence_key_text(k["key"]) not in retuned]
+    for entry in entries:
         ndim, dims, shape, r, dtype, bc, steps, kind = entry
         best, ev = tune_key(ndim, dims, shape, r, dtype, bc, steps, args.quick, kind=kind)
         torch.cuda.empty_cache()
@@ -414,7 +469,7 @@ def main():
                                  "kind": kind, "size_class": cls, "geometry": geo},
                          "candidates_timed": len(ev), "fastest": ev[:10]})
         winners.append((entry, best))
-    for dtype in ("f32", "bf16"):
+    for dtype in (("f32", "bf16") if not args.keys else ()):
         best, ev = tune_batch(dtype, quick=args.quick)
         torch.cuda.empty_cache()
         if best is None:

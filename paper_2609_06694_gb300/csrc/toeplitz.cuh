@@ -53,17 +53,27 @@ constexpr int kRows = 132;              // 128 output rows + 2 halo rows on each
 constexpr int kChunkBytes = 2176;
 static_assert(kChunkBytes >= kRows * 16 && kChunkBytes % 128 == 0, "chunk column");
 constexpr int kThreads = 192;
-constexpr int kBBytes = 1024;           // one B matrix: N32 x K16, 16-bit
+constexpr int kBBytes = 2048;           // B of one (dz, dy) pair: N64 x K16, 16-bit
 constexpr int kPad = 2048;              // guard after the B matrices
 
 __host__ __device__ constexpr int slot_bytes(int nb) { return 2 * (nb + 1) * kChunkBytes; }
-__host__ __device__ constexpr int nacc(int nb) { return nb == 4 ? 2 : 4; }
-__host__ __device__ constexpr int tmem_cols(int nb) { return nacc(nb) * nb * 32; }
-__host__ __device__ constexpr int nbmat(int dzn) { return dzn * 5 * 2; }
+// accumulators (one per output plane in flight) and tensor-memory columns: with A read from
+// shared memory by every MMA (atmem = false), 2 or 4 accumulators of nb x 32 columns; with A
+// staged in tensor memory (atmem, nb = 1), 8 accumulators in columns 0-255 and two buffers of
+// the plane's 10 A tiles (8 columns each) from column 256
+__host__ __device__ constexpr int nacc(int nb, bool atmem = false) {
+    return atmem ? 8 : (nb == 4 ? 2 : 4);
+}
+__host__ __device__ constexpr int tmem_cols(int nb, bool atmem = false) {
+    return atmem ? 512 : nacc(nb) * nb * 32;
+}
+constexpr int kACol = 256;  // first column of the A tiles (atmem)
+__host__ __device__ constexpr int nbmat(int dzn) { return dzn * 5; }
 // bytes of dynamic shared memory: slots, B matrices, guard, then the barriers and flags
-__host__ __device__ constexpr int smem_bytes(int nb, int dzn, int ns) {
-    return ns * slot_bytes(nb) + nbmat(dzn) * kBBytes + kPad + (2 * ns + 2 * nacc(nb) + 1) * 8 +
-           16 + 1024;  // + alignment slack for the 1024-byte aligned base
+__host__ __device__ constexpr int smem_bytes(int nb, int dzn, int ns, bool atmem = false) {
+    return ns * slot_bytes(nb) + nbmat(dzn) * kBBytes + kPad +
+           (2 * ns + 2 * nacc(nb, atmem) + 1) * 8 + 16 +
+           1024;  // + alignment slack for the 1024-byte aligned base
 }
 
 // No-swizzle K-major shared-memory matrix descriptor (tcgen05): start address, leading
@@ -105,6 +115,22 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+// D (tensor memory) = A * B (+ D), A from tensor memory (lane = row, K along the columns).
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Copy a 128-row x 32-byte matrix (described by a shared-memory descriptor) into tensor
+// memory: row m to lane m, its 32 bytes to 8 consecutive columns.  Ordered with the MMAs the
+// same thread issues before and after it.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;\n" ::"r"(taddr), "l"(sdesc)
+                 : "memory");
 }
 // Arrive once on the mbarrier when every MMA this thread issued so far has completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -171,16 +197,20 @@ struct ToeplitzParams {
     int phantom;            // extra arrivals the accumulator-free barriers wait for (tests)
 };
 
-// DZN = 5 (3D) or 1 (2D).  One work item (x tile, y tile, z chunk) per CTA.
-template <typename T, int NB, int DZN>
+// DZN = 5 (3D) or 1 (2D).  One work item (x tile, y tile, z chunk) per CTA.  ATMEM: the A
+// tiles of each input plane are copied once into tensor memory and every MMA of the five
+// output planes that read the plane takes A from there (five times fewer shared-memory operand
+// reads); otherwise every MMA reads A from the plane tile in shared memory.
+template <typename T, int NB, int DZN, bool ATMEM>
 __global__ void __launch_bounds__(tz::kThreads)
     toeplitz_box_kernel(const __grid_constant__ CUtensorMap map, const ToeplitzParams P,
                         const __grid_constant__ ToeplitzCoeffs<DZN * 25> cf) {
     using H = tz::Half16<T>;
     constexpr int RZ = DZN / 2;
     constexpr int SLOT = tz::slot_bytes(NB);
-    constexpr int NACC = tz::nacc(NB);
-    constexpr int COLS = tz::tmem_cols(NB);
+    static_assert(!ATMEM || NB == 1, "A in tensor memory: one block of 16 outputs per CTA");
+    constexpr int NACC = tz::nacc(NB, ATMEM);
+    constexpr int COLS = tz::tmem_cols(NB, ATMEM);
     constexpr int NBM = tz::nbmat(DZN);
     const int NS = P.stages;
 
@@ -211,19 +241,22 @@ __global__ void __launch_bounds__(tz::kThreads)
     const int nzo = min(P.z_chunk, P.z_hi - z0);  // output planes of this CTA (>= 1)
     const int nin = nzo + 2 * RZ;                  // input planes
 
-    // Toeplitz B matrices, head and tail of each coefficient (all threads)
-    for (int e = threadIdx.x; e < NBM * 512; e += blockDim.x) {
-        const int mi = e >> 9, rem = e & 511;
+    // Toeplitz B matrices, one per (dz, dy) pair: rows n = 0-31 take the first 16 columns of
+    // a block's input window (kk = 0), rows 32-63 the second (kk = 1); within each, rows 0-15
+    // the head and 16-31 the tail of each coefficient.  K-major, no swizzle: element (n, k) at
+    // (k / 8) * 1024 + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2 (all threads)
+    for (int e = threadIdx.x; e < NBM * 1024; e += blockDim.x) {
+        const int mi = e >> 10, rem = e & 1023;
         const int n = rem >> 4, k = rem & 15;
-        const int kk = mi & 1, dyi = (mi >> 1) % 5, dzi = (mi >> 1) / 5;
-        const int dx = 16 * kk + k - 8 - (n & 15);
+        const int kk = n >> 5, nn = n & 31, dyi = mi % 5, dzi = mi / 5;
+        const int dx = 16 * kk + k - 8 - (nn & 15);
         uint16_t b = 0;
         if (dx >= -2 && dx <= 2) {
             const float c = cf.c[(dzi * 5 + dyi) * 5 + dx + 2];
             const uint16_t hi = H::bits(c);
-            b = n < 16 ? hi : H::bits(c - H::value(hi));
+            b = nn < 16 ? hi : H::bits(c - H::value(hi));
         }
-        const uint32_t off = mi * tz::kBBytes + (k >> 3) * 512 + (n >> 3) * 128 + (n & 7) * 16 +
+        const uint32_t off = mi * tz::kBBytes + (k >> 3) * 1024 + (n >> 3) * 128 + (n & 7) * 16 +
                              (k & 7) * 2;
         *reinterpret_cast<uint16_t *>(gbase + (bmat - base) + off) = b;
     }
@@ -283,9 +316,69 @@ __global__ void __launch_bounds__(tz::kThreads)
         }
     } else if (warp == 1) {
         // ---- MMA issuer ----
-        if (lane == 0) {
+        if (lane == 0 && ATMEM) {
+            // input-stationary: each plane's 10 A tiles (5 row offsets x 2 K halves) are copied
+            // into tensor memory once, the slot is released as soon as the copies are done,
+            // and the plane's MMAs go to every output plane it contributes to
             constexpr uint32_t idesc = tz::instr_desc(H::kFmt, 128, 32);
-            const uint64_t bdesc0 = tz::smem_desc(bmat, 512, 128);
+            const uint64_t bdesc0 = tz::smem_desc(bmat, 1024, 128);
+            bool ok = true;
+            for (int i = 0; i < nin && ok; ++i) {
+                const int s = i % NS;
+                if (!mbar_wait_abortable(full0 + 8 * s, (i / NS) & 1, limit, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tz::tc_fence_after();
+                const uint32_t abuf = tmem + tz::kACol + (i & 1) * 80;
+                const uint64_t sdesc0 = tz::smem_desc(slots + s * SLOT, tz::kChunkBytes, 128);
+#pragma unroll
+                for (int dyi = 0; dyi < 5; ++dyi)
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+                        tz::tmem_cp_128x256b(abuf + (dyi * 2 + kk) * 8,
+                                             sdesc0 + ((2 * kk * tz::kChunkBytes + dyi * 16) >> 4));
+                tz::mma_commit(empty0 + 8 * s);  // the slot is free once the copies are done
+                // the output plane that starts with this input plane needs a free accumulator
+                if (i < nzo && i >= NACC) {
+                    if (!mbar_wait_abortable(acce0 + 8 * (i % NACC), ((i / NACC) - 1) & 1, limit,
+                                             abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tz::tc_fence_after();
+                }
+                // output plane j = i - dzi reads this plane with the (dz = dzi - 2) matrices;
+                // consecutive MMAs write different output planes
+#pragma unroll
+                for (int dyi = 0; dyi < 5; ++dyi)
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                        for (int dzi = 0; dzi < DZN; ++dzi) {
+                            const int j = i - dzi;
+                            if (j < 0 || j >= nzo) continue;
+                            tz::mma_f16_ta(tmem + (j % NACC) * 32, abuf + (dyi * 2 + kk) * 8,
+                                           bdesc0 + (((dzi * 5 + dyi) * tz::kBBytes + kk * 512) >> 4),
+                                           idesc, (dzi | dyi | kk) != 0);
+                        }
+                if (i - (DZN - 1) >= 0 && i - (DZN - 1) < nzo)  // output i - 4 is complete
+                    tz::mma_commit(accf0 + 8 * ((i - (DZN - 1)) % NACC));
+            }
+            if (!ok && !*abort_flag) {
+                latch_error(P.err, kErrTimeout);
+                *abort_flag = 1;
+            }
+            tz::mma_commit(drain);
+            mbar_wait_bounded(drain, 0, limit);
+        } else if (lane == 0) {
+            // output-stationary.  Block b of an output plane accumulates at columns
+            // (NB - 1 - b) * 32, so the accumulators of blocks p and p - 1 are adjacent in that
+            // order: the A tile of window chunk pair p feeds both with one N64 MMA whose B is
+            // the pair's whole matrix (kk = 0 rows for block p, kk = 1 rows for block p - 1)
+            constexpr uint32_t idesc32 = tz::instr_desc(H::kFmt, 128, 32);
+            constexpr uint32_t idesc64 = tz::instr_desc(H::kFmt, 128, 64);
+            const uint64_t bdesc0 = tz::smem_desc(bmat, 1024, 128);
             bool ok = true;
             for (int j = 0; j < nzo && ok; ++j) {
                 const int a = j % NACC;
@@ -306,17 +399,34 @@ __global__ void __launch_bounds__(tz::kThreads)
                     const uint64_t adesc0 = tz::smem_desc(slots + s * SLOT, tz::kChunkBytes, 128);
 #pragma unroll
                     for (int dyi = 0; dyi < 5; ++dyi) {
+                        const uint64_t bpair = bdesc0 + (((dzi * 5 + dyi) * tz::kBBytes) >> 4);
+                        const uint64_t bkk1 = bpair + (512 >> 4);  // rows 32-63
+                        if (dzi == 0 && dyi == 0) {
+                            // first terms: every block is written once by its kk = 0 MMA
+                            // before any accumulates into it (consecutive MMAs write
+                            // different blocks)
 #pragma unroll
-                        for (int b = 0; b < NB; ++b) {
+                            for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
-                            for (int kk = 0; kk < 2; ++kk) {
-                                const uint64_t adesc =
-                                    adesc0 + ((2 * (b + kk) * tz::kChunkBytes + dyi * 16) >> 4);
-                                const uint64_t bdesc =
-                                    bdesc0 + ((((dzi * 5 + dyi) * 2 + kk) * tz::kBBytes) >> 4);
-                                tz::mma_f16(dacc + b * 32, adesc, bdesc, idesc,
-                                            (dzi | dyi | kk) != 0);
-                            }
+                                for (int b = 0; b < NB; ++b)
+                                    tz::mma_f16(dacc + (NB - 1 - b) * 32,
+                                                adesc0 + ((2 * (b + kk) * tz::kChunkBytes + dyi * 16) >> 4),
+                                                kk ? bkk1 : bpair, idesc32, kk);
+                            continue;
+                        }
+                        // chunk pairs in the order 0, 2, 4, .., 1, 3, ..: consecutive MMAs
+                        // write disjoint accumulator columns
+#pragma unroll
+                        for (int q = 0; q <= NB; ++q) {
+                            const int p = 2 * q <= NB ? 2 * q : 2 * (q - NB / 2 - 1) + 1;
+                            const uint64_t adesc =
+                                adesc0 + ((2 * p * tz::kChunkBytes + dyi * 16) >> 4);
+                            if (p == 0)
+                                tz::mma_f16(dacc + (NB - 1) * 32, adesc, bpair, idesc32, 1);
+                            else if (p == NB)
+                                tz::mma_f16(dacc, adesc, bkk1, idesc32, 1);
+                            else
+                                tz::mma_f16(dacc + (NB - 1 - p) * 32, adesc, bpair, idesc64, 1);
                         }
                     }
                 }
@@ -354,7 +464,8 @@ __global__ void __launch_bounds__(tz::kThreads)
 #pragma unroll 1
             for (int b = 0; b < NB; ++b) {
                 float v[32];
-                tz::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * NB * 32 + b * 32, v);
+                tz::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * NB * 32 + (NB - 1 - b) * 32,
+                              v);
                 if (b == NB - 1) {
                     tz::tc_fence_before();
                     __syncwarp();

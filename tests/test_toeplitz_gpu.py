@@ -21,10 +21,11 @@ def _dev():
     torch.cuda.set_device(0)
 
 
-def _plan(ndim, dims, dtype, c, tile_x=16, z_chunk=0, stages=0):
+def _plan(ndim, dims, dtype, c, tile_x=16, z_chunk=0, stages=0, atmem=False):
+    """A plan on the tensor-core kernel; atmem: A staged in tensor memory (block_y = 2)."""
     plan = gs.stencil_plan(ndim, dims, "box", 2, "const", c, dtype, "dirichlet")
     gs.stencil_plan_set_variant(plan, family=gs.FAMILY_TENSOR, tile_x=tile_x, z_chunk=z_chunk,
-                                stages=stages, fuse=1)
+                                stages=stages, fuse=1, block_y=2 if atmem else 1)
     return plan
 
 
@@ -41,11 +42,11 @@ CASES = [(3, (6, 130, 40)), (3, (9, 64, 64)), (3, (3, 20, 24)), (3, (1, 7, 8)),
 
 @pytest.mark.parametrize("ndim,dims", CASES)
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-@pytest.mark.parametrize("tile_x", [16, 32, 64])
-def test_tensor_sweep_matches_oracle(ndim, dims, dtype, tile_x):
+@pytest.mark.parametrize("tile_x,atmem", [(16, False), (32, False), (64, False), (16, True)])
+def test_tensor_sweep_matches_oracle(ndim, dims, dtype, tile_x, atmem):
     offs = oracle.offsets(ndim, "box", 2)
     c = _weights(601, ndim)
-    plan = _plan(ndim, dims, dtype, c, tile_x=tile_x)
+    plan = _plan(ndim, dims, dtype, c, tile_x=tile_x, atmem=atmem)
     x, x64 = make_input(602, dims, dtype)
     xd = x.cuda()
     y = torch.empty_like(xd)
@@ -59,12 +60,13 @@ def test_tensor_sweep_matches_oracle(ndim, dims, dtype, tile_x):
     y2 = torch.empty_like(xd)
     gs.stencil_apply(plain, xd, y2, 1)
     err2 = relerr(inputs.stored_values(y2), ref)
-    print(f"{ndim}D {dims} {dtype} tile_x {tile_x}: max rel err {err:.2e} (tensor cores), "
+    print(f"{ndim}D {dims} {dtype} tile_x {tile_x} A in {'TMEM' if atmem else 'SMEM'}: "
+          f"max rel err {err:.2e} (tensor cores), "
           f"{err2:.2e} (CUDA cores)")
     assert err < TOL[dtype]
 
 
-@pytest.mark.parametrize("z_chunk,stages", [(1, 5), (2, 6), (7, 5), (3, 12), (0, 8)])
+@pytest.mark.parametrize("z_chunk,stages", [(1, 5), (2, 6), (7, 5), (3, 12), (0, 8), (9, 2)])
 def test_tensor_launch_shapes(z_chunk, stages):
     dims = (13, 140, 48)
     offs = oracle.offsets(3, "box", 2)
@@ -73,23 +75,28 @@ def test_tensor_launch_shapes(z_chunk, stages):
     xd = x.cuda()
     ref = oracle.sweep_const(x64, offs, c, "dirichlet")
     outs = []
-    for tile_x in (16, 32):
-        plan = _plan(3, dims, "bf16", c, tile_x=tile_x, z_chunk=z_chunk, stages=stages)
+    forms = [(16, False), (32, False), (16, True)] if stages >= 5 else [(16, True)]
+    for tile_x, atmem in forms:
+        plan = _plan(3, dims, "bf16", c, tile_x=tile_x, z_chunk=z_chunk, stages=stages,
+                     atmem=atmem)
         y = torch.empty_like(xd)
         gs.stencil_apply(plan, xd, y, 1)
         assert gs.stencil_sync_status(plan) == 0
         assert relerr(inputs.stored_values(y), ref) < TOL["bf16"]
         outs.append(y)
-    # the tile width changes which CTA computes a cell, not the arithmetic of the cell
-    assert torch.equal(outs[0], outs[1])
+    # the tile width and the A source change which CTA computes a cell and when, not the
+    # order of the MMAs that accumulate it
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_tensor_multi_step_and_adjoint(dtype):
+@pytest.mark.parametrize("atmem", [False, True])
+def test_tensor_multi_step_and_adjoint(dtype, atmem):
     dims = (10, 70, 56)
     offs = oracle.offsets(3, "box", 2)
     c = inputs.normalised_abs_weights(621, 125)
-    plan = _plan(3, dims, dtype, c, tile_x=32)
+    plan = _plan(3, dims, dtype, c, tile_x=16 if atmem else 32, atmem=atmem)
     x, x64 = make_input(622, dims, dtype)
     xd = x.cuda()
     y = torch.empty_like(xd)
@@ -103,13 +110,14 @@ def test_tensor_multi_step_and_adjoint(dtype):
     assert relerr(inputs.stored_values(y), ref) < TOL[dtype]
 
 
-def test_tensor_expired_wait_is_reported():
+@pytest.mark.parametrize("atmem", [False, True])
+def test_tensor_expired_wait_is_reported(atmem):
     # one phantom arrival on every "accumulator read" barrier: the MMA lane's wait for a free
     # accumulator expires once the ring of accumulators has gone round once
     dims = (12, 64, 32)
     offs = oracle.offsets(3, "box", 2)
     c = _weights(641, 3)
-    plan = _plan(3, dims, "bf16", c, tile_x=16, z_chunk=12, stages=6)
+    plan = _plan(3, dims, "bf16", c, tile_x=16, z_chunk=12, stages=6, atmem=atmem)
     x, x64 = make_input(642, dims, "bf16")
     xd = x.cuda()
     y = torch.empty_like(xd)
@@ -123,15 +131,14 @@ def test_tensor_expired_wait_is_reported():
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_tensor_384_cubed_whole_grid(dtype):
-    """384^3 zero-Dirichlet 125-point box in 16-bit storage, the tensor-core launch the
-    benchmark times, against the oracle at every cell."""
+@pytest.mark.parametrize("atmem", [False, True])
+def test_tensor_384_cubed_whole_grid(dtype, atmem):
+    """384^3 zero-Dirichlet 125-point box in 16-bit storage on the tensor cores, against the
+    oracle at every cell."""
     dims = (384, 384, 384)
     offs = oracle.offsets(3, "box", 2)
     c = _weights(2002, 3)
-    plan = gs.stencil_plan(3, dims, "box", 2, "const", c, dtype, "dirichlet")
-    gs.stencil_plan_set_variant(plan, family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0, stages=0,
-                                fuse=1)
+    plan = _plan(3, dims, dtype, c, tile_x=16, atmem=atmem)
     x = inputs.to_storage(inputs.uniform(2003, dims), dtype)
     xd = x.cuda()
     y = torch.empty_like(xd)
