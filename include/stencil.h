@@ -285,13 +285,11 @@ typedef struct {
 #define STENCIL_FAMILY_TENSOR 4  /* the radius-2 box (2D and 3D) on the tensor cores, Toeplitz
                                     packing of the x direction (Sec. 6, tensor-core mapping):
                                     f16/bf16 storage, zero Dirichlet, rows a multiple of 8
-                                    cells; tile_x = 16, 32 or 64 outputs per CTA, z_chunk
-                                    planes per CTA (0 = one wave), stages plane slots (0 =
-                                    automatic, else 5..12), block_y = 2 stages each plane's
-                                    A operand once in tensor memory (tile_x 16, stages 2..12)
-                                    instead of reading it from shared memory in every MMA
-                                    (block_y 0 or 1; other values are refused); block_x and
-                                    vec_y are ignored. Accumulates in
+                                    cells; tile_x = 16, 32 or 64 outputs per CTA, vec_y warps
+                                    issue the MMAs, each for every vec_y-th output plane (0 or
+                                    1, 2, or 4 with tile_x 64), z_chunk planes per CTA (0 = one
+                                    wave), stages plane slots (0 = automatic, else 5..12);
+                                    block_y must be 0 or 1, block_x is ignored. Accumulates in
                                     FP32 with the coefficients split into two 16-bit parts, so
                                     results equal the FP32 path to within rounding, not bit
                                     for bit */

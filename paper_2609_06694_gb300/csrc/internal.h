@@ -89,10 +89,10 @@ constexpr bool fused3d_compiled(int ndim, int shape, int radius) {
 
 // The radius-2 box on the tensor cores (toeplitz.cuh): one step per launch, 16-bit storage,
 // zero Dirichlet, rows a multiple of 8 cells; nb blocks of 16 outputs per CTA along x (1, 2
-// or 4), z_chunk output planes per CTA (0 = one wave), stages plane slots (0 = automatic; at
-// least 5 in 3D when A is read from shared memory, 2 when it is staged in tensor memory);
-// atmem: each plane's A tiles staged once in tensor memory (nb = 1 only).
-int launch_toeplitz(const StreamLaunch &L, int nb, bool atmem);
+// or 4), mw warps issuing the MMAs, each for every mw-th output plane (1 or 2; 4 with nb = 4),
+// z_chunk output planes per CTA (0 = one wave), stages plane slots (0 = automatic, else at
+// least 5 in 3D).
+int launch_toeplitz(const StreamLaunch &L, int nb, int mw);
 constexpr bool toeplitz_compiled(int ndim, int shape, int radius, int dtype) {
     return (ndim == 2 || ndim == 3) && shape == 1 && radius == 2 && (dtype == 1 || dtype == 2);
 }

@@ -182,12 +182,13 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
         if (!toeplitz_compiled(p.ndim, p.shape, p.radius, p.dtype) ||
             p.boundary != STENCIL_DIRICHLET0 || p.dims[2] % 8 != 0)
             return STENCIL_ERR_UNSUPPORTED;
-        // block_y selects where the MMAs read A: 1 (or 0) shared memory, 2 tensor memory
-        // (one 16-output block per CTA)
-        const bool atmem = v.block_y == 2;
+        // vec_y: warps issuing the MMAs, each for every vec_y-th output plane (0 or 1, 2, or
+        // 4 with 64-output tiles)
+        const int mw = v.vec_y <= 1 ? 1 : v.vec_y, nb = v.tile_x / 16;
         if ((v.tile_x != 16 && v.tile_x != 32 && v.tile_x != 64) || v.fuse != 1 ||
-            v.z_chunk < 0 || v.block_y < 0 || v.block_y > 2 || (atmem && v.tile_x != 16) ||
-            (v.stages != 0 && (v.stages < (atmem ? 2 : 5) || v.stages > 12)))
+            v.z_chunk < 0 || v.block_y < 0 || v.block_y > 1 ||
+            (v.stages != 0 && (v.stages < 5 || v.stages > 12)) || v.vec_y < 0 ||
+            (mw != 1 && mw != 2 && mw != 4) || (mw == 4 && nb != 4))
             return STENCIL_ERR_BADARG;
         return STENCIL_OK;
     }
@@ -282,7 +283,7 @@ static int launch_group(stencil_plan_s &p, const float *cf, const void *src, voi
     if (v.family == STENCIL_FAMILY_FUSED3D && k == 2 && !slab)
         return map_launch_rc(launch_fused3d(L));
     if (v.family == STENCIL_FAMILY_TENSOR)
-        return map_launch_rc(launch_toeplitz(L, v.tile_x / 16, v.block_y == 2));
+        return map_launch_rc(launch_toeplitz(L, v.tile_x / 16, v.vec_y <= 1 ? 1 : v.vec_y));
     return map_launch_rc(launch_stream(L));
 }
 

@@ -10,7 +10,7 @@ namespace gst {
 
 namespace {
 
-template <typename T, int NB, int DZN, bool ATMEM>
+template <typename T, int NB, int DZN, int MW>
 int launch_tz(const StreamLaunch &L) {
     const int ndim = L.ndim;
     const int64_t nz = ndim == 3 ? L.nz : 1;
@@ -28,12 +28,11 @@ int launch_tz(const StreamLaunch &L) {
     P.err = L.err;
     P.wait_ns = L.wait.ns;
     P.phantom = L.wait.phantom;
-    const void *kern = (const void *)toeplitz_box_kernel<T, NB, DZN, ATMEM>;
-    // ring depth: A in tensor memory frees a slot as soon as its plane is copied (4 slots);
-    // otherwise at least 5 (the input planes of one output plane in 3D), as deep as two CTAs
+    const void *kern = (const void *)toeplitz_box_kernel<T, NB, DZN, MW>;
+    constexpr int threads = tz::threads(MW);
+    // ring depth: at least 5 (the input planes of one output plane in 3D), as deep as two CTAs
     // per SM allow, else as deep as one allows
     int ns = L.stages;
-    if (ns == 0 && ATMEM) ns = DZN == 1 ? 2 : 4;
     if (ns == 0) {
         int dev = 0, per_sm = 0, optin = 0, reserved = 0;
         cudaGetDevice(&dev);
@@ -46,16 +45,15 @@ int launch_tz(const StreamLaunch &L) {
                         (tz::slot_bytes(NB) + 16);
         ns = DZN == 1 ? 2 : (two >= 6 ? std::min(two, 12) : std::min(one, 12));
     }
-    if (ns < (DZN == 1 || ATMEM ? 2 : 5) || ns > 12) return -1;
+    if (ns < (DZN == 1 ? 2 : 5) || ns > 12) return -1;
     P.stages = ns;
     // no more CTAs per SM than the tensor memory holds (512 columns), so that no CTA waits in
     // its allocation: the shared-memory request is raised to keep the others off the SM
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    const int max_ctas = 512 / tz::tmem_cols(NB, ATMEM);
-    const int smem =
-        std::max(tz::smem_bytes(NB, DZN, ns, ATMEM), per_sm / (max_ctas + 1) + 1024);
+    const int max_ctas = 512 / tz::tmem_cols(NB);
+    const int smem = std::max(tz::smem_bytes(NB, DZN, ns), per_sm / (max_ctas + 1) + 1024);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -69,7 +67,7 @@ int launch_tz(const StreamLaunch &L) {
         zc = 1;
     } else if (zc <= 0) {
         // one wave: as many z chunks per column of tiles as the resident CTAs allow
-        const int slots = resident_slots(kern, tz::kThreads, smem);
+        const int slots = resident_slots(kern, threads, smem);
         const int chunks = std::max(1, std::min(nzr, slots / std::max(1, items_xy)));
         zc = (nzr + chunks - 1) / chunks;
     }
@@ -78,31 +76,33 @@ int launch_tz(const StreamLaunch &L) {
     if (grid > 0x7fffffff) return -1;
     ToeplitzCoeffs<DZN * 25> cf;
     for (int i = 0; i < DZN * 25; ++i) cf.c[i] = L.coeffs[i];
-    toeplitz_box_kernel<T, NB, DZN, ATMEM><<<(unsigned)grid, tz::kThreads, smem, L.stream>>>(
-        map, P, cf);
+    toeplitz_box_kernel<T, NB, DZN, MW><<<(unsigned)grid, threads, smem, L.stream>>>(map, P, cf);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 template <typename T, int DZN>
-int launch_nb(const StreamLaunch &L, int nb, bool atmem) {
-    if (atmem) return nb == 1 ? launch_tz<T, 1, DZN, true>(L) : -1;
-    switch (nb) {
-    case 1: return launch_tz<T, 1, DZN, false>(L);
-    case 2: return launch_tz<T, 2, DZN, false>(L);
-    case 4: return launch_tz<T, 4, DZN, false>(L);
+int launch_nb(const StreamLaunch &L, int nb, int mw) {
+    switch (nb * 8 + mw) {
+    case 1 * 8 + 1: return launch_tz<T, 1, DZN, 1>(L);
+    case 1 * 8 + 2: return launch_tz<T, 1, DZN, 2>(L);
+    case 2 * 8 + 1: return launch_tz<T, 2, DZN, 1>(L);
+    case 2 * 8 + 2: return launch_tz<T, 2, DZN, 2>(L);
+    case 4 * 8 + 1: return launch_tz<T, 4, DZN, 1>(L);
+    case 4 * 8 + 2: return launch_tz<T, 4, DZN, 2>(L);
+    case 4 * 8 + 4: return launch_tz<T, 4, DZN, 4>(L);
     default: return -1;
     }
 }
 
 }  // namespace
 
-int launch_toeplitz(const StreamLaunch &L, int nb, bool atmem) {
+int launch_toeplitz(const StreamLaunch &L, int nb, int mw) {
     if (!toeplitz_compiled(L.ndim, L.shape, L.radius, L.dtype) || L.periodic || L.nx % 8 != 0)
         return -2;
     if (L.dtype == 2)
-        return L.ndim == 3 ? launch_nb<__nv_bfloat16, 5>(L, nb, atmem)
-                           : launch_nb<__nv_bfloat16, 1>(L, nb, atmem);
-    return L.ndim == 3 ? launch_nb<__half, 5>(L, nb, atmem) : launch_nb<__half, 1>(L, nb, atmem);
+        return L.ndim == 3 ? launch_nb<__nv_bfloat16, 5>(L, nb, mw)
+                           : launch_nb<__nv_bfloat16, 1>(L, nb, mw);
+    return L.ndim == 3 ? launch_nb<__half, 5>(L, nb, mw) : launch_nb<__half, 1>(L, nb, mw);
 }
 
 }  // namespace gst

@@ -7,17 +7,20 @@
 //     out[z, y, x0 + n] += sum_k u[z + dz, y + dy, x0 - 8 + k] * B_{dz,dy}[k, n],
 //     B_{dz,dy}[k, n] = c(dz, dy, k - 8 - n)   where |k - 8 - n| <= 2, else 0.
 // A CTA owns M = 128 consecutive output rows (y) by NB blocks of 16 outputs (x) and walks a
-// chunk of z planes.  Per output plane, block, input plane (5 in 3D) and row offset dy (5) it
-// issues two tcgen05.mma of shape M128 x N32 x K16 (the two 16-column halves of the 32-wide
-// input window of a block), so the shifted input rows are the A operand, read in place from
-// the plane tile in shared memory, and the Toeplitz matrices are the B operand.  The N = 32
-// columns hold the coefficients split into a 16-bit head and a 16-bit tail (c = hi + lo, both
-// in the storage type), so the product keeps the coefficients to about 16 significant bits
-// while the inputs are exact; the FP32 accumulators (tensor memory) are summed head + tail in
-// the epilogue and rounded once to the storage type.
+// chunk of z planes.  The shifted input rows are the A operand, read in place from the plane
+// tile in shared memory (one 16-column half of the window per MMA, K = 16), and the Toeplitz
+// matrices are the B operand.  Each B row block holds the coefficients split into a 16-bit
+// head and a 16-bit tail (c = hi + lo, both in the storage type), so the product keeps the
+// coefficients to about 16 significant bits while the inputs are exact; the FP32 accumulators
+// (tensor memory) are summed head + tail in the epilogue and rounded once to the storage type.
+// The window halves of neighbouring blocks overlap: the half that is the second half of block
+// p - 1 is the first of block p, so one M128 x N64 x K16 MMA (B = both halves' matrices)
+// serves both blocks, whose accumulators sit side by side (block b at columns (NB-1-b) * 32).
+// Per output plane, input plane (5 in 3D) and row offset dy (5) that is NB + 1 MMAs.
 //
 // Dense packing pays a density penalty: 32 K-elements per output and (dz, dy) pair against 5
-// useful taps, twice for the head/tail split.
+// useful taps, twice for the head/tail split.  The MMAs are narrow (N <= 64), and their rate
+// is set by how fast they are issued: MW warps issue them, each for every MW-th output plane.
 //
 // Shared-memory layout of a plane tile (the A operand).  Rows y0-2 .. y0+129 (132 rows) of
 // the input window x0-8 .. x0-8+16(NB+1), stored as columns of 16-byte chunks: chunk c (8
@@ -29,13 +32,16 @@
 // chunk column is one 3D TMA tensor copy (box 8 x 132 x 1) from the grid, zero-filling outside
 // it (zero Dirichlet); the copies of a plane complete on one mbarrier.
 //
-// Warp roles (6 warps): warp 0 issues the TMA copies, warp 1 owns the tensor memory and one
-// of its lanes issues the MMAs, warps 2-5 read the accumulators (each warp its 32 lanes of
-// tensor memory) and store the outputs.  Slots and accumulators change hands through
-// mbarriers; tcgen05.commit signals MMA completion.  Every wait is bounded: on expiry the CTA
+// Warp roles (5 + MW warps): warp 0 issues the TMA copies, warps 1..MW issue the MMAs (one
+// lane each; warp 1 also owns the tensor memory), the last 4 warps read the accumulators
+// (each warp its 32 lanes of tensor memory) and store the outputs.  Slots and accumulators
+// change hands through mbarriers; tcgen05.commit signals MMA completion; a slot is refilled
+// once every issuing warp has released its plane.  Every wait is bounded: on expiry the CTA
 // latches STENCIL_ERR_TIMEOUT, raises its abort flag, waits (bounded) for the copies and MMAs
 // it issued, frees its tensor memory and returns.
 #pragma once
+
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -52,28 +58,22 @@ constexpr int kRows = 132;              // 128 output rows + 2 halo rows on each
 // shared memory starts on a 128-byte boundary
 constexpr int kChunkBytes = 2176;
 static_assert(kChunkBytes >= kRows * 16 && kChunkBytes % 128 == 0, "chunk column");
-constexpr int kThreads = 192;
+constexpr int kThreads = 192;     // producer, one MMA warp, 4 epilogue warps
+constexpr int kMaxThreads = 288;  // with 4 MMA warps
+__host__ __device__ constexpr int threads(int mw) { return 32 * (5 + mw); }
 constexpr int kBBytes = 2048;           // B of one (dz, dy) pair: N64 x K16, 16-bit
 constexpr int kPad = 2048;              // guard after the B matrices
 
 __host__ __device__ constexpr int slot_bytes(int nb) { return 2 * (nb + 1) * kChunkBytes; }
-// accumulators (one per output plane in flight) and tensor-memory columns: with A read from
-// shared memory by every MMA (atmem = false), 2 or 4 accumulators of nb x 32 columns; with A
-// staged in tensor memory (atmem, nb = 1), 8 accumulators in columns 0-255 and two buffers of
-// the plane's 10 A tiles (8 columns each) from column 256
-__host__ __device__ constexpr int nacc(int nb, bool atmem = false) {
-    return atmem ? 8 : (nb == 4 ? 2 : 4);
-}
-__host__ __device__ constexpr int tmem_cols(int nb, bool atmem = false) {
-    return atmem ? 512 : nacc(nb) * nb * 32;
-}
-constexpr int kACol = 256;  // first column of the A tiles (atmem)
+// accumulators (one per output plane in flight, nb x 32 columns each) and tensor-memory
+// columns
+constexpr int kNacc = 4;
+__host__ __device__ constexpr int tmem_cols(int nb) { return kNacc * nb * 32; }
 __host__ __device__ constexpr int nbmat(int dzn) { return dzn * 5; }
 // bytes of dynamic shared memory: slots, B matrices, guard, then the barriers and flags
-__host__ __device__ constexpr int smem_bytes(int nb, int dzn, int ns, bool atmem = false) {
-    return ns * slot_bytes(nb) + nbmat(dzn) * kBBytes + kPad +
-           (2 * ns + 2 * nacc(nb, atmem) + 1) * 8 + 16 +
-           1024;  // + alignment slack for the 1024-byte aligned base
+__host__ __device__ constexpr int smem_bytes(int nb, int dzn, int ns) {
+    return ns * slot_bytes(nb) + nbmat(dzn) * kBBytes + kPad + (2 * ns + 2 * kNacc + 1) * 8 +
+           16 + 1024;  // + alignment slack for the 1024-byte aligned base
 }
 
 // No-swizzle K-major shared-memory matrix descriptor (tcgen05): start address, leading
@@ -115,22 +115,6 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
-}
-// D (tensor memory) = A * B (+ D), A from tensor memory (lane = row, K along the columns).
-__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
-                                           uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-// Copy a 128-row x 32-byte matrix (described by a shared-memory descriptor) into tensor
-// memory: row m to lane m, its 32 bytes to 8 consecutive columns.  Ordered with the MMAs the
-// same thread issues before and after it.
-__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
-    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;\n" ::"r"(taddr), "l"(sdesc)
-                 : "memory");
 }
 // Arrive once on the mbarrier when every MMA this thread issued so far has completed.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -197,20 +181,18 @@ struct ToeplitzParams {
     int phantom;            // extra arrivals the accumulator-free barriers wait for (tests)
 };
 
-// DZN = 5 (3D) or 1 (2D).  One work item (x tile, y tile, z chunk) per CTA.  ATMEM: the A
-// tiles of each input plane are copied once into tensor memory and every MMA of the five
-// output planes that read the plane takes A from there (five times fewer shared-memory operand
-// reads); otherwise every MMA reads A from the plane tile in shared memory.
-template <typename T, int NB, int DZN, bool ATMEM>
-__global__ void __launch_bounds__(tz::kThreads)
+// DZN = 5 (3D) or 1 (2D).  One work item (x tile, y tile, z chunk) per CTA.  MW warps issue
+// the MMAs, each for every MW-th output plane of the CTA.
+template <typename T, int NB, int DZN, int MW>
+__global__ void __launch_bounds__(tz::kMaxThreads)
     toeplitz_box_kernel(const __grid_constant__ CUtensorMap map, const ToeplitzParams P,
                         const __grid_constant__ ToeplitzCoeffs<DZN * 25> cf) {
     using H = tz::Half16<T>;
     constexpr int RZ = DZN / 2;
     constexpr int SLOT = tz::slot_bytes(NB);
-    static_assert(!ATMEM || NB == 1, "A in tensor memory: one block of 16 outputs per CTA");
-    constexpr int NACC = tz::nacc(NB, ATMEM);
-    constexpr int COLS = tz::tmem_cols(NB, ATMEM);
+    static_assert(MW >= 1 && MW <= tz::kNacc, "MMA warps");
+    constexpr int NACC = tz::kNacc;
+    constexpr int COLS = tz::tmem_cols(NB);
     constexpr int NBM = tz::nbmat(DZN);
     const int NS = P.stages;
 
@@ -263,13 +245,13 @@ __global__ void __launch_bounds__(tz::kThreads)
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, MW);
         }
         for (int a = 0; a < NACC; ++a) {
             mbar_init(accf0 + 8 * a, 1);
             mbar_init(acce0 + 8 * a, 4 + P.phantom);
         }
-        mbar_init(drain, 1);
+        mbar_init(drain, MW);
         *abort_flag = 0;
         mbar_init_fence();
     }
@@ -314,64 +296,10 @@ __global__ void __launch_bounds__(tz::kThreads)
             for (int i = max(0, issued - NS); i < issued; ++i)
                 mbar_wait_bounded(full0 + 8 * (i % NS), (i / NS) & 1, limit);
         }
-    } else if (warp == 1) {
-        // ---- MMA issuer ----
-        if (lane == 0 && ATMEM) {
-            // input-stationary: each plane's 10 A tiles (5 row offsets x 2 K halves) are copied
-            // into tensor memory once, the slot is released as soon as the copies are done,
-            // and the plane's MMAs go to every output plane it contributes to
-            constexpr uint32_t idesc = tz::instr_desc(H::kFmt, 128, 32);
-            const uint64_t bdesc0 = tz::smem_desc(bmat, 1024, 128);
-            bool ok = true;
-            for (int i = 0; i < nin && ok; ++i) {
-                const int s = i % NS;
-                if (!mbar_wait_abortable(full0 + 8 * s, (i / NS) & 1, limit, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tz::tc_fence_after();
-                const uint32_t abuf = tmem + tz::kACol + (i & 1) * 80;
-                const uint64_t sdesc0 = tz::smem_desc(slots + s * SLOT, tz::kChunkBytes, 128);
-#pragma unroll
-                for (int dyi = 0; dyi < 5; ++dyi)
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk)
-                        tz::tmem_cp_128x256b(abuf + (dyi * 2 + kk) * 8,
-                                             sdesc0 + ((2 * kk * tz::kChunkBytes + dyi * 16) >> 4));
-                tz::mma_commit(empty0 + 8 * s);  // the slot is free once the copies are done
-                // the output plane that starts with this input plane needs a free accumulator
-                if (i < nzo && i >= NACC) {
-                    if (!mbar_wait_abortable(acce0 + 8 * (i % NACC), ((i / NACC) - 1) & 1, limit,
-                                             abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tz::tc_fence_after();
-                }
-                // output plane j = i - dzi reads this plane with the (dz = dzi - 2) matrices;
-                // consecutive MMAs write different output planes
-#pragma unroll
-                for (int dyi = 0; dyi < 5; ++dyi)
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-                        for (int dzi = 0; dzi < DZN; ++dzi) {
-                            const int j = i - dzi;
-                            if (j < 0 || j >= nzo) continue;
-                            tz::mma_f16_ta(tmem + (j % NACC) * 32, abuf + (dyi * 2 + kk) * 8,
-                                           bdesc0 + (((dzi * 5 + dyi) * tz::kBBytes + kk * 512) >> 4),
-                                           idesc, (dzi | dyi | kk) != 0);
-                        }
-                if (i - (DZN - 1) >= 0 && i - (DZN - 1) < nzo)  // output i - 4 is complete
-                    tz::mma_commit(accf0 + 8 * ((i - (DZN - 1)) % NACC));
-            }
-            if (!ok && !*abort_flag) {
-                latch_error(P.err, kErrTimeout);
-                *abort_flag = 1;
-            }
-            tz::mma_commit(drain);
-            mbar_wait_bounded(drain, 0, limit);
-        } else if (lane == 0) {
+    } else if (warp <= MW) {
+        // ---- MMA issuers, A read from shared memory: warp w (1..MW) runs the output planes
+        // j = w - 1, w - 1 + MW, ... ----
+        if (lane == 0) {
             // output-stationary.  Block b of an output plane accumulates at columns
             // (NB - 1 - b) * 32, so the accumulators of blocks p and p - 1 are adjacent in that
             // order: the A tile of window chunk pair p feeds both with one N64 MMA whose B is
@@ -379,8 +307,22 @@ __global__ void __launch_bounds__(tz::kThreads)
             constexpr uint32_t idesc32 = tz::instr_desc(H::kFmt, 128, 32);
             constexpr uint32_t idesc64 = tz::instr_desc(H::kFmt, 128, 64);
             const uint64_t bdesc0 = tz::smem_desc(bmat, 1024, 128);
+            const int w = warp - 1;
+            // a slot is refilled once each issuing warp has released its plane: this warp
+            // releases plane p when none of its later output planes reads it (planes the
+            // producer never refills, p >= nin - NS, are not released)
+            int released = 0;
+            const int lim = nin - NS;
+            auto release_upto = [&](int p_end, bool after_mmas) {
+                for (const int e = min(p_end, lim); released < e; ++released) {
+                    const uint32_t bar = empty0 + 8 * (released % NS);
+                    if (after_mmas) tz::mma_commit(bar);  // once this warp's MMAs are done
+                    else mbar_arrive(bar);
+                }
+            };
+            release_upto(w < nzo ? w : nin, false);
             bool ok = true;
-            for (int j = 0; j < nzo && ok; ++j) {
+            for (int j = w; j < nzo && ok; j += MW) {
                 const int a = j % NACC;
                 if (j >= NACC &&
                     !mbar_wait_abortable(acce0 + 8 * a, ((j / NACC) - 1) & 1, limit, abort_flag)) {
@@ -432,7 +374,7 @@ __global__ void __launch_bounds__(tz::kThreads)
                 }
                 if (!ok) break;
                 tz::mma_commit(accf0 + 8 * a);
-                tz::mma_commit(empty0 + 8 * (j % NS));  // input plane j is used by no later output
+                release_upto(j + MW < nzo ? j + MW : nin, true);
             }
             if (!ok && !*abort_flag) {
                 latch_error(P.err, kErrTimeout);
@@ -444,7 +386,7 @@ __global__ void __launch_bounds__(tz::kThreads)
         }
         __syncwarp();
     } else {
-        // ---- epilogue: warps 2..5, tensor-memory lanes 32 * (warp % 4) ----
+        // ---- epilogue: warps MW + 1 .. MW + 4, tensor-memory lanes 32 * (warp % 4) ----
         const int q = warp & 3;
         const int y = y0 + q * 32 + lane;
         for (int j = 0; j < nzo; ++j) {

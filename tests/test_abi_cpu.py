@@ -413,11 +413,11 @@ def test_tensor_variant_validation():
     c125 = np.ones(125) / 125
     p = gs.stencil_plan(3, (8, 16, 16), "box", 2, "const", c125, "bf16", "dirichlet")
     gs.stencil_plan_set_variant(p, family=gs.FAMILY_TENSOR, tile_x=32, z_chunk=0, stages=0,
-                                fuse=1, block_y=1)
+                                fuse=1, block_y=1, vec_y=2)  # two warps issue the MMAs
     assert gs.stencil_plan_get_variant(p)["family"] == gs.FAMILY_TENSOR
     p2 = gs.stencil_plan(2, (40, 24), "box", 2, "const", np.ones(25), "f16", "dirichlet")
     gs.stencil_plan_set_variant(p2, family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0, stages=0,
-                                fuse=1, block_y=1)
+                                fuse=1, block_y=1, vec_y=0)
     for dtype, bc, dims, shape, r, n in (("f32", "dirichlet", (8, 16, 16), "box", 2, 125),
                                          ("bf16", "periodic", (8, 16, 16), "box", 2, 125),
                                          ("bf16", "dirichlet", (8, 16, 20), "box", 2, 125),
@@ -426,14 +426,16 @@ def test_tensor_variant_validation():
         q = gs.stencil_plan(3, dims, shape, r, "const", np.ones(n), dtype, bc)
         with pytest.raises(gs.StencilError) as e:
             gs.stencil_plan_set_variant(q, family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0,
-                                        stages=0, fuse=1, block_y=1)
+                                        stages=0, fuse=1, block_y=1, vec_y=1)
         assert e.value.code == -2
-    gs.stencil_plan_set_variant(p, family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0, stages=2,
-                                fuse=1, block_y=2)  # A staged in tensor memory
+    gs.stencil_plan_set_variant(p, family=gs.FAMILY_TENSOR, tile_x=64, z_chunk=0, stages=0,
+                                fuse=1, block_y=1, vec_y=4)  # four warps issue the MMAs
     for bad in (dict(tile_x=48), dict(tile_x=16, stages=4), dict(tile_x=16, stages=13),
-                dict(tile_x=16, fuse=2), dict(tile_x=16, z_chunk=-1), dict(block_y=3),
-                dict(block_y=2, tile_x=32), dict(block_y=2, stages=1)):
-        kw = dict(family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0, stages=0, fuse=1, block_y=1)
+                dict(tile_x=16, fuse=2), dict(tile_x=16, z_chunk=-1), dict(block_y=2),
+                dict(vec_y=4), dict(vec_y=3, tile_x=64), dict(vec_y=8, tile_x=64),
+                dict(vec_y=-1)):
+        kw = dict(family=gs.FAMILY_TENSOR, tile_x=16, z_chunk=0, stages=0, fuse=1, block_y=1,
+                  vec_y=1)
         kw.update(bad)
         with pytest.raises(gs.StencilError) as e:
             gs.stencil_plan_set_variant(p, **kw)
