@@ -337,9 +337,10 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
-def tuned_cuda_core_variant(ndim, dims, shape, radius, dtype, bc):
-    """The fastest non-tensor-core variant the autotuner timed for this workload, from the
-    package's dispatch evidence (None if the key is not there)."""
+def tuned_variant(ndim, dims, shape, radius, dtype, bc, family=None):
+    """The fastest variant the autotuner timed for this workload (of `family` if given, else
+    of any family but the tensor cores), from the package's dispatch evidence; None if the
+    key or such a variant is not there."""
     import paper_2609_06694_gb300 as gs
     path = os.path.join(os.path.dirname(gs.api.DISPATCH_MAP), "dispatch_evidence.json")
     try:
@@ -353,7 +354,8 @@ def tuned_cuda_core_variant(ndim, dims, shape, radius, dtype, bc):
                 kk.get("shape") == shape and kk.get("radius") == radius and
                 kk.get("dtype") == dtype and kk.get("boundary") == bc):
             for e in k["fastest"]:
-                if e["variant"]["family"] != gs.FAMILY_TENSOR:
+                fam = e["variant"]["family"]
+                if (fam == family) if family is not None else (fam != gs.FAMILY_TENSOR):
                     return e["variant"]
     return None
 
@@ -599,7 +601,13 @@ def measure_metric_ratios(W3=None, wave=True):
     c27, _ = inputs.normalised_sum_weights(2002, 27)
     for name, shape, c, by in (("star1", "star", c7, 7), ("box", "box", c27, 7)):
         plain = gs.stencil_plan(3, dims, shape, 1, "const", c, "f32", "periodic")
-        gs.stencil_plan_set_variant(plain, family=gs.FAMILY_STREAM)
+        if gs.stencil_plan_get_variant(plain)["family"] != gs.FAMILY_STREAM:
+            # the map's entry for this key may be the fused kernel: single sweeps on the
+            # fastest streaming variant the autotuner timed (else a tile tuned for the box)
+            best = tuned_variant(3, dims, shape, 1, "f32", "periodic", gs.FAMILY_STREAM) or dict(
+                family=gs.FAMILY_STREAM, block_x=32, block_y=4, vec_y=2, z_chunk=32, fuse=1,
+                tile_x=0, tile_y=0, stages=0)
+            gs.stencil_plan_set_variant(plain, **best)
         fused = gs.stencil_plan(3, dims, shape, 1, "const", c, "f32", "periodic")
         gs.stencil_plan_set_variant(fused, family=gs.FAMILY_FUSED3D, block_x=32, block_y=by,
                                     vec_y=2, z_chunk=64, fuse=2, tile_x=0, tile_y=0, stages=0)
@@ -643,7 +651,7 @@ def measure_metric_ratios(W3=None, wave=True):
                                         tile_x=64, z_chunk=0, stages=0, fuse=1)
         # the CUDA-core side runs the fastest CUDA-core variant the autotuner timed for this
         # key (its evidence file), else the library default
-        best = tuned_cuda_core_variant(3, dims, "box", 2, dt, "dirichlet")
+        best = tuned_variant(3, dims, "box", 2, dt, "dirichlet")
         if best is not None:
             gs.stencil_plan_set_variant(core, **best)
         elif gs.stencil_plan_get_variant(core)["family"] == gs.FAMILY_TENSOR:

@@ -333,7 +333,8 @@ class Batch:
 
 def stencil_batch_plan(items, steps, tile_y=0, tile_x=0, fuse=0) -> Batch:
     """items: sequence of (Plan, in_tensor, out_tensor); all 2D const plans.  tile_y, tile_x,
-    fuse: the launch shape (0: the library's default)."""
+    fuse: the launch shape (all 0: the dispatch map's shape for the storage type, else the
+    library default for any field left 0)."""
     lib = _lib()
     arr = (stencil_batch_item * len(items))()
     for i, (plan, inp, out) in enumerate(items):
@@ -343,9 +344,14 @@ def stencil_batch_plan(items, steps, tile_y=0, tile_x=0, fuse=0) -> Batch:
         arr[i].in_ = inp.data_ptr()
         arr[i].out = out.data_ptr()
     h = ctypes.c_void_p()
-    _check(lib.stencil_batch_plan_tiles(ctypes.byref(h), arr, len(items), int(steps),
-                                        int(tile_y), int(tile_x), int(fuse)),
-           "stencil_batch_plan")
+    if tile_y == 0 and tile_x == 0 and fuse == 0:
+        # the launch shape of the dispatch map's "batch" line for the storage type
+        _check(lib.stencil_batch_plan(ctypes.byref(h), arr, len(items), int(steps)),
+               "stencil_batch_plan")
+    else:
+        _check(lib.stencil_batch_plan_tiles(ctypes.byref(h), arr, len(items), int(steps),
+                                            int(tile_y), int(tile_x), int(fuse)),
+               "stencil_batch_plan")
     return Batch(h.value, list(items))
 
 

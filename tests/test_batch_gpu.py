@@ -141,7 +141,7 @@ def test_full_batch_256_grids_20_steps(dtype):
           f"FP64, {worst_emu:.2e} vs per-step rounding")
 
 
-@pytest.mark.parametrize("tiles", [(0, 0, 0), (16, 120, 3)])
+@pytest.mark.parametrize("tiles", [(0, 0, 0), (16, 120, 2)])  # 3 steps: two groups
 def test_barrier_timeout_is_reported_and_context_survives(tiles):
     specs = [(64, 128, "star", 1, "f32", "dirichlet"), (50, 70, "box", 1, "f32", "periodic")]
     batch, grids = make_batch(specs, 3, tiles)
