@@ -16,13 +16,7 @@ template <typename T, int SHAPE, int R> static int launch_fused2d_t(const Fused2
     if (L.block_threads < 32 || L.block_threads > 256 || L.block_threads % 32) return -1;
     const size_t smem = fused2d_smem_bytes(L.tile_x, L.tile_y, R, L.steps);
     if (smem > 227 * 1024) return -2;
-    static size_t smem_set = 0;
-    if (smem > 48 * 1024 && smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return -4;
-        smem_set = smem;
-    }
+    if (!smem_opt_in(reinterpret_cast<const void *>(kern), smem, false)) return -4;
     ConstCoeffs<NPTS> cf;
     for (int i = 0; i < NPTS; ++i) cf.c[i] = L.coeffs[i];
     const int64_t tiles_x = (L.nx + L.tile_x - 1) / L.tile_x;

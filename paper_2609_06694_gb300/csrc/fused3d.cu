@@ -46,15 +46,7 @@ template <typename T, int SHAPE, int R> static int launch_fused3d_t(const Stream
     const size_t smem = K::smem_bytes(by, ns);
     if (smem > 227 * 1024) return -2;
     p.nstage = ns;
-    static size_t smem_set = 0;
-    if (smem > 48 * 1024 && smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-            return -4;
-        smem_set = smem;
-    }
+    if (!smem_opt_in(reinterpret_cast<const void *>(kern), smem, true)) return -4;
     const int64_t total = (int64_t)p.tiles_x * p.tiles_y * nz;
     int64_t work;
     if (L.z_chunk > 0) {

@@ -27,6 +27,12 @@ void status_release(int slot, bool used);
 int *status_word(int slot);
 int status_take(int slot, cudaStream_t s);
 
+// Raises the kernel's dynamic shared-memory limit on the current device to at least `smem`
+// bytes (and with max_carveout asks for the largest shared-memory carveout).  The attribute is
+// per device: the calls are recorded per (device, kernel) under a mutex, so any host thread
+// may launch on any device.  False if the runtime refuses.
+bool smem_opt_in(const void *kern, size_t smem, bool max_carveout);
+
 // One launch of the streaming sweep kernel (one time step).
 struct StreamLaunch {
     int ndim;                // 2 or 3

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include <cudaTypedefs.h>
 
@@ -35,28 +36,37 @@ template <typename T> constexpr CUtensorMapDataType tensor_dtype() {
     else return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
 }
 
-// CTAs of a kernel that can be resident on the whole GPU at once (cached per kernel and
-// launch shape).
+// CTAs of a kernel that can be resident on the whole current device at once (cached per
+// device, kernel and launch shape, under a mutex).
 inline int resident_slots(const void *kern, int threads, size_t smem) {
     struct Entry {
+        int dev;
         const void *k;
         int t;
         size_t s;
         int slots;
     };
-    static Entry cache[64];
+    static Entry cache[128];
     static int ncache = 0;
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lk(mu);
     for (int i = 0; i < ncache; ++i)
-        if (cache[i].k == kern && cache[i].t == threads && cache[i].s == smem) return cache[i].slots;
-    int dev = 0, sms = 0, per = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        if (cache[i].dev == dev && cache[i].k == kern && cache[i].t == threads &&
+            cache[i].s == smem)
+            return cache[i].slots;
+    int sms = 0, per = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     const int slots = per * sms;
-    if (ncache < 64) cache[ncache++] = {kern, threads, smem, slots};
+    if (ncache < 128) cache[ncache++] = {dev, kern, threads, smem, slots};
     return slots;
 }
 

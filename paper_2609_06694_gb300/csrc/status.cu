@@ -104,4 +104,34 @@ int status_take(int slot, cudaStream_t s) {
     return v;
 }
 
+bool smem_opt_in(const void *kern, size_t smem, bool max_carveout) {
+    if (smem <= 48 * 1024) return true;
+    struct Entry {
+        int dev;
+        const void *kern;
+        size_t smem;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry &e : done)
+        if (e.dev == dev && e.kern == kern && e.smem >= smem) return true;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        (max_carveout && cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    for (Entry &e : done)
+        if (e.dev == dev && e.kern == kern) {
+            e.smem = smem;
+            return true;
+        }
+    done.push_back({dev, kern, smem});
+    return true;
+}
+
 }  // namespace gst

@@ -30,15 +30,7 @@ int launch_stream_go(const StreamLaunch &L, StreamParams<T> &p,
     p.nstage = ring_stages(L.stages, NDIM, reinterpret_cast<const void *>(kern), threads,
                            K::slot_bytes(by, SIDE));
     const size_t smem = K::smem_bytes(by, SIDE, p.nstage);
-    static size_t smem_set = 0;  // per instantiation
-    if (smem > 48 * 1024 && smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-            return -4;
-        smem_set = smem;
-    }
+    if (!smem_opt_in(reinterpret_cast<const void *>(kern), smem, true)) return -4;
     // Work split: z_chunk > 0 gives every CTA z_chunk planes; z_chunk == 0 sizes the grid to
     // the CTAs that fit on the GPU at once (a multiple of the SM count) and gives each an equal
     // share of the (tile, z) planes.

@@ -54,11 +54,7 @@ int launch_tz(const StreamLaunch &L) {
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     const int max_ctas = 512 / tz::tmem_cols(NB);
     const int smem = std::max(tz::smem_bytes(NB, DZN, ns), per_sm / (max_ctas + 1) + 1024);
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return -2;
-    }
+    if (!smem_opt_in(kern, (size_t)smem, false)) return -2;
     const int nzr = P.z_hi - P.z_lo;
     if (nzr <= 0) return 0;
     const int items_xy = P.tiles_x * P.tiles_y;

@@ -50,13 +50,7 @@ int launch_var_t(const VarLaunch &L) {
     if (nblocks > INT32_MAX) return -2;
     const size_t smem = (size_t)NSLOT * PITCH * (by + 2 * R) * sizeof(T);
     auto kern = var_sweep_kernel<T, NDIM, SHAPE, R, ADJ>;
-    static size_t smem_set = 0;
-    if (smem > 48 * 1024 && smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-            return -4;
-        smem_set = smem;
-    }
+    if (!smem_opt_in(reinterpret_cast<const void *>(kern), smem, false)) return -4;
     kern<<<(unsigned)nblocks, dim3(BX, by), smem, L.stream>>>(p);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -4;
@@ -118,15 +112,7 @@ template <typename T, int NDIM, int VY> int launch_divkgrad_nd(const VarLaunch &
     p.nstage = std::max(2 * K::RZ + 2, ring_stages(0, NDIM, reinterpret_cast<const void *>(kern),
                                                    threads, 2 * K::field_bytes(by)));
     const size_t smem = K::smem_bytes(by, p.nstage);
-    static size_t smem_set = 0;
-    if (smem > 48 * 1024 && smem > smem_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-            return -4;
-        smem_set = smem;
-    }
+    if (!smem_opt_in(reinterpret_cast<const void *>(kern), smem, true)) return -4;
     // z chunks of z_chunk planes per CTA; z_chunk == 0 sizes the grid to the CTAs that fit on
     // the GPU at once and gives each an equal share of the (tile, z) planes (one wave, no tail)
     const int64_t total = (int64_t)p.tiles_x * p.tiles_y * nz;
