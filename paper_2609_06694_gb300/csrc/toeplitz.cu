@@ -1,6 +1,5 @@
 // Host launcher of the tensor-core (Toeplitz) radius-2 box sweep (toeplitz.cuh).
 #include <algorithm>
-#include <cstring>
 
 #include "internal.h"
 #include "ring_launch.cuh"

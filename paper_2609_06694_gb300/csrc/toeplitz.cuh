@@ -58,8 +58,8 @@ constexpr int kRows = 132;              // 128 output rows + 2 halo rows on each
 // shared memory starts on a 128-byte boundary
 constexpr int kChunkBytes = 2176;
 static_assert(kChunkBytes >= kRows * 16 && kChunkBytes % 128 == 0, "chunk column");
-constexpr int kThreads = 192;     // producer, one MMA warp, 4 epilogue warps
-constexpr int kMaxThreads = 288;  // with 4 MMA warps
+// threads of a CTA: the producer warp, mw MMA warps and 4 epilogue warps (at most 4 MMA warps)
+constexpr int kMaxThreads = 288;
 __host__ __device__ constexpr int threads(int mw) { return 32 * (5 + mw); }
 constexpr int kBBytes = 2048;           // B of one (dz, dy) pair: N64 x K16, 16-bit
 constexpr int kPad = 2048;              // guard after the B matrices
