@@ -410,9 +410,10 @@ def profile_case(args):
         rc = gs.stencil_sync_status(plan)
     elif args.only == "divkgrad":
         n = args.grid if args.grid != N else 384
-        plan = gs.stencil_plan(3, (n, n, n), "star", 1, "divkgrad", None, "f32", "dirichlet")
-        k = inputs.to_storage(inputs.lognormal_k(3002, (n, n, n)), "f32").cuda()
-        u = inputs.to_storage(inputs.uniform(3001, (n, n, n)), "f32").cuda()
+        dt = args.dtype
+        plan = gs.stencil_plan(3, (n, n, n), "star", 1, "divkgrad", None, dt, "dirichlet")
+        k = inputs.to_storage(inputs.lognormal_k(3002, (n, n, n)), dt).cuda()
+        u = inputs.to_storage(inputs.uniform(3001, (n, n, n)), dt).cuda()
         y = torch.empty_like(u)
         for _ in range(args.warmup + args.steps):
             gs.stencil_apply_var(plan, u, [k], y, 1)
@@ -817,6 +818,8 @@ def main():
     ap.add_argument("--no-ratios", action="store_true",
                     help="skip the adjoint / batched / div(k grad u) / wave measurements that "
                          "the bench line carries under metric_ratios")
+    ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32",
+                    help="storage type of the div(k grad u) profiling case")
     ap.add_argument("--only", choices=["star", "box", "divkgrad", "var", "wave", "batch", "tensor",
                                        "fused3d", "reaction", "box2"],
                     default=None,
