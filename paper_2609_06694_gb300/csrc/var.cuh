@@ -422,8 +422,9 @@ __global__ void __launch_bounds__(DivkKernel<T, NDIM, VY>::MAX_THREADS + 32)
                     load_span<T, -1, VX + 1, -1>(su + kofs + i0, k0);
                     // Each face adds (k_c + k_n) (u_n - u_c); the sum is halved at the end (exact,
                     // so this equals the half-face form bit for bit).  A neighbour outside a
-                    // Dirichlet grid has u = 0 and k = k_c.  ALLIN: no neighbour of this thread's
-                    // cells is outside the grid, so no face needs a select.
+                    // Dirichlet grid has u = 0 and k = k_c (see the ghost-face term below).
+                    // ALLIN: no face needs a select (the only form used: the ghost faces are
+                    // completed afterwards).
                     auto compute = [&](auto allin_c) {
                         constexpr bool ALLIN = decltype(allin_c)::value;
                         auto face = [&](int i, float un, float kn, bool inside) {
@@ -472,13 +473,23 @@ __global__ void __launch_bounds__(DivkKernel<T, NDIM, VY>::MAX_THREADS + 32)
                             face(i, u0[i], k0[i], inm);
                         }
                     };
-                    const bool all_in =
-                        periodic || (ox > 0 && ox + VX < nx && oy > 0 && oy + 1 < ny &&
-                                     (NDIM == 2 || (zo > 0 && zo + 1 < nz)));
-                    if (all_in)
-                        compute(std::true_type{});
-                    else
-                        compute(std::false_type{});
+                    // Every face is taken as if both cells were inside the grid: the ring
+                    // zero-fills whatever lies outside a Dirichlet grid, so a face towards a
+                    // ghost comes out as (k_c + 0) (0 - u_c), half its value (k_c + k_c)(0 - u_c).
+                    // The missing half, -k_c u_c per ghost face, is added afterwards for the
+                    // cells at the grid's faces; interior rows skip it.
+                    compute(std::true_type{});
+                    if (!periodic) {
+                        const int byz = (oy == 0) + (oy == ny - 1) +
+                                        (NDIM == 3 ? (zo == 0) + (zo == nz - 1) : 0);
+                        if (byz != 0 || ox == 0 || ox + VX >= nx) {
+#pragma unroll
+                            for (int i = 0; i < VX; ++i) {
+                                const int b = byz + (ox + i == 0) + (ox + i == nx - 1);
+                                acc[i] = fmaf(-(float)b * k0[i + 1], u0[i + 1], acc[i]);
+                            }
+                        }
+                    }
                 }
             }  // rows of the thread
             release_plane();  // plane zo - RZ has been read for the last time (whole warp)
