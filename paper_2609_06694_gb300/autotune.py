@@ -111,6 +111,19 @@ def divkgrad_candidates(dtype, quick=False):
     return out
 
 
+def var_candidates(dtype, quick=False):
+    """General variable-coefficient sweeps: one output row per thread, rows of threads and z
+    chunk (0 = whole columns)."""
+    bx = 128 // (16 // (4 if dtype == "f32" else 2))
+    heights = (2, 4, 6, 8, 12, 14) if not quick else (2, 4, 8)
+    out = []
+    for by, zc in itertools.product(heights, (0, 16, 32, 64, 128)):
+        if bx * by <= 224 and (bx * by) % 32 == 0:
+            out.append(dict(family=gs.FAMILY_STREAM, block_x=bx, block_y=by, vec_y=1,
+                            z_chunk=zc, fuse=1, tile_x=0, tile_y=0, stages=0))
+    return out
+
+
 def tensor_candidates(ndim, quick=False):
     """Tensor-core (Toeplitz) variants of the radius-2 box: 16, 32 or 64 outputs per CTA
     along x, 1, 2 or 4 warps issuing the MMAs (vec_y), z chunk (0 = one wave)."""
@@ -154,6 +167,16 @@ def _problem(ndim, dims, shape, radius, dtype, bc, kind):
         plan = gs.stencil_plan(ndim, dims, "star", 1, "divkgrad", None, dtype, bc)
         k = inputs.to_storage(inputs.lognormal_k(4, dims), dtype).cuda()
         return plan, (lambda p, n: gs.stencil_apply_var(p, x, [k], y, n)), 3
+    if kind == "var":
+        # one variant serves the forward and the adjoint sweep: both are timed
+        plan = gs.stencil_plan(ndim, dims, shape, radius, "var", None, dtype, bc)
+        npts = _npts(ndim, shape, radius)
+        w = [inputs.to_storage(inputs.uniform(9 + i, dims), dtype).cuda() for i in range(npts)]
+
+        def run(p, n):
+            gs.stencil_apply_var(p, x, w, y, n)
+            gs.stencil_apply_adjoint_var(p, x, w, y, n)
+        return plan, run, 2 * (npts + 2)
     c = inputs.normalised_abs_weights(7, _npts(ndim, shape, radius))
     plan = gs.stencil_plan(ndim, dims, shape, radius, "const", c, dtype, bc)
     return plan, (lambda p, n: gs.stencil_apply(p, x, y, n)), 2
@@ -167,6 +190,8 @@ def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=pri
     plan, run, bytes_per_cell = _problem(ndim, dims, shape, radius, dtype, bc, kind)
     if kind == "divkgrad":
         cands = divkgrad_candidates(dtype, quick)
+    elif kind == "var":
+        cands = var_candidates(dtype, quick)
     else:
         cands = stream_candidates(ndim, shape, radius, dtype, quick)
         if ndim == 2 and steps > 1:
@@ -226,6 +251,7 @@ def tuning_set(quick=False):
             s.append((3, big, shape, r, "f32", bc, 1, "const"))
     for dtype in ("f32",) if quick else ("f32", "f16", "bf16"):
         s.append((3, (384, 384, 384), "star", 1, dtype, "dirichlet", 1, "divkgrad"))
+        s.append((3, (384, 384, 384), "star", 1, dtype, "dirichlet", 1, "var"))
     if quick:
         return s
     for dtype in ("f16", "bf16"):

@@ -297,6 +297,8 @@ def test_library_missing_fails_loudly(monkeypatch, tmp_path):
 def _plan_for(ndim, dims, shape, r, dtype, bc, kind):
     if kind == "divkgrad":
         return gs.stencil_plan(ndim, dims, "star", 1, "divkgrad", None, dtype, bc)
+    if kind == "var":
+        return gs.stencil_plan(ndim, dims, shape, r, "var", None, dtype, bc)
     return gs.stencil_plan(ndim, dims, shape, r, "const",
                            np.ones(len(oracle.offsets(ndim, shape, r))), dtype, bc)
 
@@ -312,6 +314,8 @@ def test_autotuner_candidates_are_variants_the_library_accepts():
         plan = _plan_for(ndim, dims, shape, r, dtype, bc, kind)
         if kind == "divkgrad":
             cands = autotune.divkgrad_candidates(dtype)
+        elif kind == "var":
+            cands = autotune.var_candidates(dtype)
         elif ndim == 2 and steps > 1:
             cands = autotune.fused2d_candidates(r, steps)
         else:
