@@ -383,7 +383,8 @@ def ncu_evidence(entry, variant, log=print):
         kern = "batch_persistent"
     else:
         spec = json.dumps({"key": list(entry), "variant": variant})
-        kern = "divkgrad" if entry[7] == "divkgrad" else KERNEL_REGEX[variant["family"]]
+        kern = {"divkgrad": "divkgrad", "var": "var_sweep"}.get(entry[7],
+                                                               KERNEL_REGEX[variant["family"]])
     replay_cmd = [sys.executable, "-m", "paper_2609_06694_gb300.autotune", "--replay", spec]
     # the same command runs to completion without ncu before it is captured
     plain = subprocess.run(replay_cmd, capture_output=True, text=True,
