@@ -355,7 +355,7 @@ def test_committed_dispatch_map_selects_its_entries():
     gs.stencil_load_dispatch_map(path)
     shapes = {0: "star", 1: "box", 2: "diamond"}
     dtypes = {0: "f32", 1: "f16", 2: "bf16"}
-    kinds = {0: "const", 2: "divkgrad"}
+    kinds = {0: "const", 1: "var", 2: "divkgrad"}
     names = ["family", "block_x", "block_y", "vec_y", "z_chunk", "fuse", "tile_x", "tile_y",
              "stages"]
     try:
