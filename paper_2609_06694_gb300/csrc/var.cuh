@@ -224,11 +224,16 @@ __global__ void __launch_bounds__(256) var_sweep_kernel(const __grid_constant__ 
             const int gz = NDIM == 3 ? wrap_or_flag(zo - dz, nz, true, ok) : 0;
             const int gy = wrap_or_flag(oy - dy, ny, true, ok);
             const T *base = p.w[idx] + (size_t)gz * pstride + (size_t)gy * nx;
+            if (dx == 0) {
+                // no shift along x: the thread's cells of the source row, one vector
+                load_cells<T, VX>(base + ox, vec, nvalid, w);
+            } else {
 #pragma unroll
-            for (int i = 0; i < VX; ++i) {
-                bool okx = true;
-                const int gx = wrap_or_flag(ox + i - dx, nx, true, okx);
-                w[i] = Storage<T>::to_float(__ldg(base + gx));
+                for (int i = 0; i < VX; ++i) {
+                    bool okx = true;
+                    const int gx = wrap_or_flag(ox + i - dx, nx, true, okx);
+                    w[i] = Storage<T>::to_float(__ldg(base + gx));
+                }
             }
         }
     };
