@@ -46,9 +46,10 @@ def stream_candidates(ndim, shape, radius, dtype, quick=False):
     # ring depth: 0 fills the shared memory the resident CTAs leave; 4 is the shallow ring
     stages = [0] if ndim == 2 else ([0] if quick else [0, 4])
     for vy in vys:
-        # consumer threads per CTA (plus the producer warp): up to 224, or 256 for 3D stars
-        # of radius >= 3 with one row per thread
-        tmax = 256 if (ndim == 3 and shape == "star" and radius >= 3 and vy == 1) else 224
+        # consumer threads per CTA (plus the producer warp): up to 224, or for 3D stars of
+        # radius >= 3 256 with one row per thread and 448 with two rows per thread in f32
+        wide = ndim == 3 and shape == "star" and radius >= 3
+        tmax = 256 if (wide and vy == 1) else 448 if (wide and vy == 2 and es == 4) else 224
         heights = (1, 2, 3, 4, 6, 7, 8, 12, 14, 15) if not quick else (2, 4, 7)
         bys = [b for b in heights if 32 <= bx * b <= tmax and (bx * b) % 32 == 0]
         for by, zc, ns in itertools.product(bys, zcs, stages):

@@ -54,8 +54,10 @@ struct StreamLaunch {
 // Returns 0, or a negative STENCIL_ERR_* code.  One per storage type and dimension.
 // Most consumer threads of a streaming kernel's CTA (kept in step with
 // StreamKernel::MAX_THREADS); the CTA adds one producer warp.
-constexpr int stream_max_threads(int ndim, int shape, int radius, int vec_y) {
-    return (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 1) ? 256 : 224;
+constexpr int stream_max_threads(int ndim, int shape, int radius, int vec_y, int dtype) {
+    return (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 1)                ? 256
+           : (ndim == 3 && shape == 0 && radius >= 3 && vec_y == 2 && dtype == 0) ? 448
+                                                                                  : 224;
 }
 
 // Defined in stream_<dtype>_<ndim>d_<shape>.cu.

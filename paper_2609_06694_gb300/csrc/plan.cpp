@@ -155,7 +155,7 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
     if (v.family == STENCIL_FAMILY_STREAM) {
         // tiles are 128 cells wide: one 16-byte vector of cells per thread along x
         if (v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
-            v.block_x * v.block_y > stream_max_threads(p.ndim, p.shape, p.radius, v.vec_y) ||
+            v.block_x * v.block_y > stream_max_threads(p.ndim, p.shape, p.radius, v.vec_y, p.dtype) ||
             (v.block_x * v.block_y) % 32 != 0)
             return STENCIL_ERR_BADARG;
         if (!stream_vy_compiled(p.ndim, p.shape, p.radius, v.vec_y))

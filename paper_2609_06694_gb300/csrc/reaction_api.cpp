@@ -25,7 +25,7 @@ static int reaction_step(stencil_plan_s &p, const void *src, void *dst, float dt
         z_chunk = v.z_chunk;
         stages = v.stages;
     }
-    const int cap = stream_max_threads(p.ndim, p.shape, p.radius, 1) / bx;
+    const int cap = stream_max_threads(p.ndim, p.shape, p.radius, 1, p.dtype) / bx;
     by = std::max(1, std::min(by, cap));
     while ((bx * by) % 32) --by;
     StreamLaunch L;

@@ -226,14 +226,17 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
         const RingPiece q = wk.piece_at(w);
         w += q.z_end - q.z_begin;
         // Chunks a periodic grid wraps into the tile: every chunk of the rows above the grid
-        // (rows < lo_row) and below it (rows >= hi_row), then, in the rows between, the chunks
-        // left of x = 0 (chunks < lo_chk) and right of nx (chunks >= hi_chk).
+        // (rows < lo_row) and of the first R rows below it (rows >= hi_row), then, in the rows
+        // between, the chunks left of x = 0 (chunks < lo_chk) and the first chunk right of nx
+        // (chunk hi_chk).  Rows further below and chunks further right feed only outputs
+        // outside the grid, which are never stored: they keep the copy's zero fill (a ragged
+        // last tile row would otherwise patch most of its plane).
         const int lo_row = max(0, R - q.y0);
         const int hi_row = min(rows, max(0, ny - (q.y0 - R)));
         const int lo_chk = max(0, (A - q.x0 + A - 1) / A);
         const int hi_chk = min(CPR, max(0, (nx - (q.x0 - A) + A - 1) / A));
-        const int nrow_oob = lo_row + (rows - hi_row);
-        const int nwc = lo_chk + (CPR - hi_chk);
+        const int nrow_oob = lo_row + min(rows - hi_row, R);
+        const int nwc = lo_chk + min(CPR - hi_chk, 1);
         const int npatch = nrow_oob * CPR + (hi_row - lo_row) * nwc;
         const int sbits = ring_side_bits(src.use_side, q.x0, q.y0, nx, ny, TX, wk.TY, R, A);
         int mode;

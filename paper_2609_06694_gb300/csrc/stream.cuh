@@ -206,9 +206,14 @@ struct StreamKernel {
     // SM sub-partition, which keeps the register cap at 255.  Wide-halo 3D stars with one row
     // per thread may take 8 consumer warps: their 288-thread bound leaves the compiler room
     // for the 72 registers of three resident CTAs (a 512-thread bound made it squeeze to 64
-    // registers and spill).
+    // registers and spill).  With two rows per thread in f32 they may take 14 (one CTA per SM,
+    // 28-row tiles: 8 halo rows on 28 instead of 14 -- 0.191 against 0.215 ms for a 512^3
+    // zero-Dirichlet radius-4 star); the 480-thread bound caps the registers at 136, above the
+    // 116-119 those kernels use.
     static constexpr int MAX_THREADS =
-        (NDIM == 3 && SHAPE == kStar && R >= 3 && VY == 1) ? 256 : 224;
+        (NDIM == 3 && SHAPE == kStar && R >= 3 && VY == 1)                        ? 256
+        : (NDIM == 3 && SHAPE == kStar && R >= 3 && VY == 2 && sizeof(T) == 4) ? 448
+                                                                                : 224;
     static_assert(R <= A, "x halo must fit in one 16-byte chunk");
 
     // needed |dx| for window row wr (union over the thread's rows and every dz); -1 = unused

@@ -334,14 +334,19 @@ def test_autotuner_candidates_are_variants_the_library_accepts():
 
 
 def test_streaming_thread_caps():
-    # 3D stars of radius >= 3 with one row per thread may take 8 warps of consumers, every
-    # other streaming variant 7; the CTA adds the producer warp
+    # 3D stars of radius >= 3 with one row per thread may take 8 warps of consumers, with two
+    # rows per thread in f32 14 (one CTA per SM, taller tiles), every other streaming variant
+    # 7; the CTA adds the producer warp
     p = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "periodic")
     gs.stencil_plan_set_variant(p, block_x=32, block_y=8, vec_y=1)
-    for by, vy in ((9, 1), (8, 2)):
+    for by, vy in ((9, 1), (15, 2), (8, 4)):
         with pytest.raises(gs.StencilError):
             gs.stencil_plan_set_variant(p, block_x=32, block_y=by, vec_y=vy)
-    gs.stencil_plan_set_variant(p, block_x=32, block_y=7, vec_y=2)
+    gs.stencil_plan_set_variant(p, block_x=32, block_y=14, vec_y=2)
+    h = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "bf16", "periodic")
+    gs.stencil_plan_set_variant(h, block_x=16, block_y=14, vec_y=2)
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(h, block_x=16, block_y=16, vec_y=2)
     b = gs.stencil_plan(3, (64, 64, 64), "box", 1, "const", np.ones(27), "bf16", "periodic")
     gs.stencil_plan_set_variant(b, block_x=16, block_y=14, vec_y=2)
     with pytest.raises(gs.StencilError):
