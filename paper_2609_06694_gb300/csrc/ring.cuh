@@ -17,6 +17,7 @@ namespace gst {
 
 constexpr int kMaxStages = 16;   // ring slots
 constexpr int kMaxPatches = 256; // wrapped 16-byte chunks patched per plane
+constexpr int kSideRowBytes = 32;  // a row of a side array: two 16-byte chunks
 constexpr unsigned long long kRingWaitNs = 2000000000ull;  // default bound on a wait: 2 s
 
 // Shared-memory layout: nstage slots of NF fields, then full/empty/tma mbarriers, the abort
@@ -28,10 +29,12 @@ struct RingLayout {
     __host__ __device__ static constexpr uint32_t field_size(int pitch, int rows, int es) {
         return (uint32_t)(((size_t)pitch * rows * es + 127) / 128 * 128);
     }
-    // the side arrays of a slot: the left and then the right 16-byte halo chunk of every row,
-    // each array starting on a 128-byte boundary (tensor-copy destinations)
+    // the side arrays of a slot: for every row, the two 16-byte chunks left of the tile (the
+    // second one is its x halo) and then the two right of it (the first one is the halo), each
+    // array starting on a 128-byte boundary (tensor-copy destinations); 32-byte rows put every
+    // fourth row on a 128-byte boundary, where a split copy of the wrapped rows may start
     __host__ __device__ static constexpr uint32_t side_half(int rows) {
-        return (uint32_t)((16 * rows + 127) / 128 * 128);
+        return (uint32_t)((kSideRowBytes * rows + 127) / 128 * 128);
     }
     __host__ __device__ static constexpr uint32_t side_size(int rows) {
         return 2 * side_half(rows);
@@ -160,6 +163,11 @@ struct RingWork {
 // are 16-byte aligned and the driver could encode them, one 3D tensor map per field with the
 // box (PITCH, rows, 1).  With use_side (one field, periodic), side_tmap is a second map of the
 // same field with the box (A, rows, 1): one 16-byte column chunk of every row.
+// With ysplit (one field, periodic), ymaps are six more maps of the field for the tile rows
+// at the y ends: [0] box (PITCH, rows - R) -- the top tile row's rows from y = 0, [1] box
+// (PITCH, hb + R) -- the bottom tile row's rows from y0 - R to the grid's end (hb: its output
+// rows), [2] box (PITCH, R) -- the R wrapped rows; [3], [4], [5] the same three boxes two
+// chunks wide (2A) for the side arrays (use_side only).
 template <typename T, int NF> struct RingSource {
     const CUtensorMap *tmap;       // NF maps (kernel parameters)
     const CUtensorMap *side_tmap;  // the side map (use_side only)
@@ -167,18 +175,34 @@ template <typename T, int NF> struct RingSource {
     int nx, ny, nz;
     bool periodic, aligned, use_tma, use_side;
     int rows;
+    const CUtensorMap *ymaps = nullptr;  // the y-split maps (ysplit != 0 only)
+    int ysplit = 0;  // bit 0: the top tile row takes split copies, bit 1: the bottom one
 };
+
+// Whether a tile of a periodic grid takes its wrapped rows by split tensor copies (ysplit
+// bits set by the host where the split lands on a 128-byte boundary of the slot): 1 = the top
+// tile row (rows above y = 0 wrap), 2 = the bottom one (rows from ny wrap), 0 = neither.
+__device__ __forceinline__ int ring_ysplit(int ysplit, int y0, int ny, int TY, int R) {
+    if ((ysplit & 1) && y0 == 0) return 1;
+    if ((ysplit & 2) && y0 >= R && y0 + TY + R > ny) return 2;
+    return 0;
+}
 
 // Which x halo chunks of a piece come from the slot's side arrays: bit 0 the left chunk (the
 // tile starts at x = 0, so the chunk wraps to x = nx - A), bit 1 the right one (the tile ends
-// at x = nx, so it wraps to x = 0).  Only periodic tiles whose rows all lie inside the grid and
+// at x = nx, so it wraps to x = 0); a side copy takes two chunks per row (x = nx - 2A and
+// x = 0, 2A wide).  Only periodic tiles whose rows all lie inside the grid and
 // whose width is whole qualify: the tensor copy of the plane zero-fills those chunks in the
 // slot, a second tensor copy of the wrapped column fills the side array alongside it on the
 // same barrier, and the consumer lanes at the tile's ends read the side array instead -- the
-// producer never touches the plane again.  Producer and consumers evaluate the same rule.
+// producer never touches the plane again.  Tiles at the y ends qualify too where their
+// wrapped rows come by split copies (ysplit_kind != 0): their side arrays then take split
+// copies as well.  Producer and consumers evaluate the same rule.
 __device__ __forceinline__ int ring_side_bits(bool use_side, int x0, int y0, int nx, int ny,
-                                              int TX, int TY, int R, int A) {
-    if (!use_side || y0 < R || y0 + TY + R > ny || nx < A) return 0;
+                                              int TX, int TY, int R, int A,
+                                              int ysplit_kind = 0) {
+    if (!use_side || nx < 2 * A) return 0;
+    if (ysplit_kind == 0 && (y0 < R || y0 + TY + R > ny)) return 0;
     const bool right = x0 + TX + A > nx;
     if (right && x0 + TX != nx) return 0;  // a partial tile: the wrap lands inside the tile
     return (x0 == 0 ? 1 : 0) | (right ? 2 : 0);
@@ -196,6 +220,12 @@ __device__ __forceinline__ int ring_side_bits(bool use_side, int x0, int y0, int
 //    "tma" and "empty" barriers in turn), the lanes copy the wrapped 16-byte chunks (whole rows
 //    above or below the grid, single chunks left or right of it) over the zero fill with
 //    cp.async and arrive on the full barrier when those have landed.
+//  mode 6, split TMA: a periodic tile at a y end (ring_ysplit) whose columns need no wrap, or
+//    wrap into side arrays: two tensor copies on the full barrier -- the rows inside the grid
+//    and, into the slot rows next to them, the R wrapped rows (top: grid rows ny - R .. ny - 1
+//    into slot rows 0 .. R - 1; bottom: grid rows 0 .. R - 1 after the last grid row) -- so
+//    nothing is copied twice and nothing waits for a copy to land.  The bottom tile row loads
+//    only its hb + 2R needed rows.  Side arrays, if any, take the same split, two chunks wide.
 //  mode 3, bulk rows: tiles with more wrapped chunks than the patch list holds (grids
 //    narrower than a tile): one bulk copy per contiguous segment of each row.
 //  mode 1, cp.async: no tensor map: 16-byte chunks of whole rows, wrapping or zero-filling.
@@ -238,10 +268,13 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
         const int nrow_oob = lo_row + min(rows - hi_row, R);
         const int nwc = lo_chk + min(CPR - hi_chk, 1);
         const int npatch = nrow_oob * CPR + (hi_row - lo_row) * nwc;
-        const int sbits = ring_side_bits(src.use_side, q.x0, q.y0, nx, ny, TX, wk.TY, R, A);
+        const int yk = NF == 1 ? ring_ysplit(src.ysplit, q.y0, ny, wk.TY, R) : 0;
+        const int sbits = ring_side_bits(src.use_side, q.x0, q.y0, nx, ny, TX, wk.TY, R, A, yk);
+        const bool x_inside = q.x0 >= A && q.x0 + TX + A <= nx;
         int mode;
         if (!src.use_tma) mode = src.aligned ? 1 : 0;
         else if (!periodic || npatch == 0) mode = 2;
+        else if (yk != 0 && (x_inside || sbits != 0)) mode = 6;
         else if (sbits != 0) mode = 5;
         else if (npatch <= kMaxPatches && hi_row >= lo_row) mode = 4;
         else mode = 3;
@@ -298,7 +331,7 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
                     fence_proxy_async_shared();  // consumers' reads of this slot come first
                     const uint32_t tb = mode == 4 ? g.tma_u32 + 8u * pos.slot : bar;
                     const uint32_t side_bytes =
-                        mode == 5 ? (uint32_t)(__popc(sbits) * rows * 16) : 0u;
+                        mode == 5 ? (uint32_t)(__popc(sbits) * rows * kSideRowBytes) : 0u;
                     mbar_arrive_expect_tx(tb, NF * plane_bytes + side_bytes);
                     const int zc = (NDIM == 3) ? (periodic ? gz : zi) : 0;
 #pragma unroll
@@ -306,10 +339,10 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
                         tma_load_3d(sbase + f * g.field_bytes, &src.tmap[f], q.x0 - A, q.y0 - R,
                                     zc, tb);
                     if (mode == 5) {
-                        // the wrapped columns: left chunk from x = nx - A, right one from x = 0
+                        // the wrapped columns: left chunks from x = nx - 2A, right ones from 0
                         const uint32_t side = sbase + g.side_off;
                         if (sbits & 1)
-                            tma_load_3d(side, src.side_tmap, nx - A, q.y0 - R, zc, tb);
+                            tma_load_3d(side, src.side_tmap, nx - 2 * A, q.y0 - R, zc, tb);
                         if (sbits & 2)
                             tma_load_3d(side + RingLayout::side_half(rows), src.side_tmap, 0,
                                         q.y0 - R, zc, tb);
@@ -318,6 +351,41 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
                     mbar_arrive(bar);
                 }
                 if (mode == 4) ++unpub;
+            } else if (mode == 6) {
+                // top: wrapped rows from ny - R into slot rows [0, R), grid rows from 0 into
+                // [R, rows); bottom: grid rows from y0 - R into [0, hb + R), wrapped rows from 0
+                // into [hb + R, hb + 2R); the side arrays alike.  Every split lies on a 128-byte
+                // boundary (host-checked).
+                if (lane == 0) {
+                    const int zc = (NDIM == 3) ? gz : 0;
+                    const int hb = ny - q.y0;  // bottom: output rows of the tile
+                    const int split = yk == 1 ? R : hb + R;  // first row of the second copy
+                    const int nrows = yk == 1 ? rows : hb + 2 * R;
+                    const uint32_t row_bytes = (uint32_t)(PITCH * ES);
+                    fence_proxy_async_shared();  // consumers' reads of this slot come first
+                    mbar_arrive_expect_tx(
+                        bar, (uint32_t)nrows * (row_bytes + __popc(sbits) * kSideRowBytes));
+                    // the first copy from y_a into row 0, the second from y = 0 (the top's
+                    // rows inside the grid, the bottom's wrapped rows) into row `split`
+                    const int y_a = yk == 1 ? ny - R : q.y0 - R;
+                    const int y_b = 0;
+                    const CUtensorMap *ma = &src.ymaps[yk == 1 ? 2 : 1];
+                    const CUtensorMap *mb = &src.ymaps[yk == 1 ? 0 : 2];
+                    tma_load_3d(sbase, ma, q.x0 - A, y_a, zc, bar);
+                    tma_load_3d(sbase + (uint32_t)split * row_bytes, mb, q.x0 - A, y_b, zc, bar);
+                    const uint32_t side = sbase + g.side_off;
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        if (!((sbits >> k) & 1)) continue;
+                        const uint32_t sd = side + (uint32_t)k * RingLayout::side_half(rows);
+                        const int xs = k == 0 ? nx - 2 * A : 0;
+                        tma_load_3d(sd, ma + 3, xs, y_a, zc, bar);
+                        tma_load_3d(sd + (uint32_t)split * kSideRowBytes, mb + 3, xs, y_b, zc,
+                                    bar);
+                    }
+                } else {
+                    mbar_arrive(bar);
+                }
             } else if (mode == 3) {
                 // every smem row is one to a few contiguous, 16-byte aligned segments of a
                 // (wrapped) grid row: the lanes take the rows and copy the segments in bulk

@@ -132,7 +132,8 @@ template <int NPTS> struct ConstCoeffs {
 
 template <typename T> struct StreamParams {
     CUtensorMap tmap;       // 3D (x, y, z) map of `in`, box (128 + 2A, TY + 2R, 1)
-    CUtensorMap side_tmap;  // the same grid, box (A, TY + 2R, 1) (use_side only)
+    CUtensorMap side_tmap;  // the same grid, box (2A, TY + 2R, 1) (use_side only)
+    CUtensorMap ymap[6];    // y-split maps of periodic y-end tiles (ring.cuh; ysplit only)
     const T *in;
     T *out;
     int nx, ny, nz;     // 2D grids: nz = 1
@@ -142,6 +143,7 @@ template <typename T> struct StreamParams {
     int work;           // planes per CTA (flattened tile x z sequence)
     int use_tma;        // 1 = tensor-map loads (tmap describes `in`)
     int use_side;       // 1 = x-wrapped halo chunks of edge tiles by side copies (periodic)
+    int ysplit;         // y-end tile rows by split copies: bit 0 the top row, bit 1 the bottom
     int nstage;         // ring slots, 2 .. kMaxStages
     int z_lo, z_cnt;    // output planes [z_lo, z_lo + z_cnt) (3D; 0, 1 for 2D)
     int *err;           // device status word (may be null)
@@ -303,6 +305,8 @@ __global__ void __launch_bounds__(
         src.aligned = aligned;
         src.use_tma = p.use_tma != 0;
         src.rows = rows;
+        src.ymaps = p.ymap;
+        src.ysplit = p.ysplit;
         ring_produce<T, 1, NDIM, R, A, PITCH, TX>(g, src, wk, p.err, lane);
         return;
     }
@@ -320,18 +324,18 @@ __global__ void __launch_bounds__(
         else return cf.c[idx];
     };
     const int thr_off = (ty * VY) * PITCH + A + tx * VX;  // element offset of the thread's base
-    // side arrays, in elements from a slot's side base: the thread's first row in the left
-    // array, shifted so that window position -A is chunk element 0; in the right array,
-    // shifted so that window position VX is chunk element 0
-    const int sl_off = (ty * VY) * A + A;
-    const int sr_off = (int)(RingLayout::side_half(rows) / sizeof(T)) + (ty * VY) * A - VX;
+    // side arrays (rows of two chunks, 2A elements), in elements from a slot's side base: the
+    // thread's first row in the left array, shifted so that window position -A is the row's
+    // second chunk; in the right array, shifted so that window position VX is the row's first
+    const int sl_off = (ty * VY) * (2 * A) + 2 * A;
+    const int sr_off = (int)(RingLayout::side_half(rows) / sizeof(T)) + (ty * VY) * (2 * A) - VX;
     bool failed = false;
 
     RingPos pos;  // ring position of the next plane
     // Where window positions < 0 (the chunk left of the thread's cells) and >= VX (the chunk
     // right of them) of window row wr come from: lb + wr * ls and rb + wr * rs -- the plane's
     // own row (stride PITCH), or for the lanes at the ends of an x-edge tile a side array
-    // (stride A).  Set per piece (strides) and per plane (bases).
+    // (stride 2A).  Set per piece (strides) and per plane (bases).
     int ls = PITCH, rs = PITCH;
     bool use_l = false, use_r = false;
     const T *lb = nullptr, *rb = nullptr;
@@ -372,11 +376,12 @@ __global__ void __launch_bounds__(
         // the lanes at the ends of an x-edge tile read their wrapped halo chunk from a side array
         if constexpr (SIDE) {
             const int sbits =
-                ring_side_bits(p.use_side != 0, q.x0, q.y0, nx, ny, TX, TY, R, A);
+                ring_side_bits(p.use_side != 0, q.x0, q.y0, nx, ny, TX, TY, R, A,
+                               ring_ysplit(p.ysplit, q.y0, ny, TY, R));
             use_l = (sbits & 1) && tx == 0;
             use_r = (sbits & 2) && tx == K::BX - 1;
-            ls = use_l ? A : PITCH;
-            rs = use_r ? A : PITCH;
+            ls = use_l ? 2 * A : PITCH;
+            rs = use_r ? 2 * A : PITCH;
         }
 
         // output addressing, hoisted

@@ -97,9 +97,32 @@ int launch_stream_t(const StreamLaunch &L,
                     : 0;
     // periodic grids: the wrapped x halo chunks of edge tiles by a second map (one chunk wide)
     p.use_side = (p.use_tma && L.periodic &&
-                  encode_plane_map<T>(&p.side_tmap, L.in, nx, ny, nz, K::A, rows))
+                  encode_plane_map<T>(&p.side_tmap, L.in, nx, ny, nz, 2 * K::A, rows))
                      ? 1
                      : 0;
+
+    // periodic tile rows at the y ends: their wrapped rows by split tensor copies (ring.cuh,
+    // mode 6) where each split lands on a 128-byte boundary of the slot (and of the side
+    // arrays, 32-byte rows), the top row of tiles needs no bottom wrap (ny >= TY + 2R) and
+    // only the last row of tiles wraps at the bottom (its hb output rows >= R)
+    p.ysplit = 0;
+    if (p.use_tma && L.periodic && p.tiles_y >= 2 && ny >= TY + 2 * R) {
+        const int64_t hb = ny - (int64_t)(p.tiles_y - 1) * TY;
+        const int64_t row_bytes = (int64_t)K::PITCH * (int64_t)sizeof(T);
+        auto fits = [&](int64_t split) {
+            return (split * row_bytes) % 128 == 0 &&
+                   (!p.use_side || (split * kSideRowBytes) % 128 == 0);
+        };
+        auto maps = [&](int k, int box_rows) {
+            return encode_plane_map<T>(&p.ymap[k], L.in, nx, ny, nz, K::PITCH, box_rows) &&
+                   (!p.use_side || encode_plane_map<T>(&p.ymap[k + 3], L.in, nx, ny, nz,
+                                                       2 * K::A, box_rows));
+        };
+        if (hb >= R && maps(2, R)) {
+            if (fits(R) && maps(0, TY + R)) p.ysplit |= 1;
+            if (fits(hb + R) && maps(1, (int)hb + R)) p.ysplit |= 2;
+        }
+    }
 
     ConstCoeffs<NPTS> cf;
     for (int i = 0; i < NPTS; ++i) cf.c[i] = L.coeffs[i];

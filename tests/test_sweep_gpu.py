@@ -133,6 +133,67 @@ def test_periodic_whole_tile_widths(dtype, shape, r):
         assert relerr(gpu_apply(plan, x), oracle.sweep_const(x64, offs, c, "periodic")) < TOL[dtype]
 
 
+def _split_rows(ny, ty, r, pitch_bytes):
+    """Which y-end tile rows of a periodic grid take split tensor copies (the rows inside the
+    grid and the R wrapped rows as two copies, at 128-byte boundaries of the slot): the same
+    rule as the library's launcher, restated for the test's coverage checks."""
+    tiles_y = -(-ny // ty)
+    hb = ny - (tiles_y - 1) * ty
+    if tiles_y < 2 or ny < ty + 2 * r or hb < r:
+        return set()
+    out = set()
+    if (r * pitch_bytes) % 128 == 0:
+        out.add("top")
+    if ((hb + r) * pitch_bytes) % 128 == 0:
+        out.add("bottom")
+    return out
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("ndim,dims,shape,r,block_y,want", [
+    # want: the split tile rows in f32, in bf16 (the split must land on 128 bytes)
+    (3, (12, 134, 384), "star", 4, 7, ({"top", "bottom"}, {"top"})),  # x-inner and corners
+    (3, (10, 134, 128), "star", 4, 7, ({"top", "bottom"}, {"top"})),  # one tile column
+    (3, (12, 140, 256), "star", 4, 7, ({"top"}, {"top", "bottom"})),
+    (3, (9, 92, 256), "star", 4, 14, ({"top", "bottom"}, None)),      # 28-row f32 tiles
+    (3, (11, 70, 256), "box", 2, 4, ({"bottom"}, {"bottom"})),        # R = 2
+    (2, (134, 384), "star", 4, 7, ({"top", "bottom"}, {"top"})),
+])
+def test_periodic_split_copies(dtype, ndim, dims, shape, r, block_y, want):
+    # periodic tile rows at the y ends take their wrapped rows by a second tensor copy into
+    # the slot rows next to the first (no patching after the copy lands); tiles that also wrap
+    # in x fill their side arrays with cp.async.  Against the oracle, and bit for bit against
+    # the same sweep of a misaligned input view (element loader, no tensor copies)
+    es = 4 if dtype == "f32" else 2
+    bx, by = (32, block_y) if es == 4 else (16, 2 * block_y)
+    vy = 2
+    if ndim == 2:
+        by = min(by, 224 // bx)
+    ty = by * vy
+    pitch_bytes = (128 + 2 * (16 // es)) * es
+    want = want[0 if es == 4 else 1]
+    if want is None:
+        pytest.skip("16-bit two-row tiles take at most 14 rows of 16 threads")
+    assert _split_rows(dims[-2], ty, r, pitch_bytes) == want
+    offs = oracle.offsets(ndim, shape, r)
+    c = seeded_weights(71, len(offs))
+    plan = gs.stencil_plan(ndim, dims, shape, r, "const", c, dtype, "periodic")
+    gs.stencil_plan_set_variant(plan, family=1, block_x=bx, block_y=by, vec_y=vy,
+                                z_chunk=4, stages=0, fuse=1)
+    x, x64 = make_input(72, dims, dtype)
+    got = gpu_apply(plan, x)
+    assert relerr(got, oracle.sweep_const(x64, offs, c, "periodic")) < TOL[dtype], dims
+    # the same input at a 4-byte offset: rows not 16-byte aligned, element loads
+    n = x.numel()
+    buf = torch.empty(n + 8, dtype=x.dtype, device="cuda")
+    xm = buf[2:2 + n].view(dims)
+    xm.copy_(x.cuda())
+    ym = torch.empty(dims, dtype=x.dtype, device="cuda")
+    gs.stencil_apply(plan, xm, ym, 1)
+    assert gs.stencil_sync_status(plan) == 0
+    assert np.array_equal(inputs.stored_values(ym), got)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("shape,r,block_y,vec_y", [("star", 4, 8, 1), ("star", 4, 7, 2),
                                                    ("star", 4, 4, 2), ("star", 2, 3, 2),
