@@ -261,11 +261,15 @@ typedef struct {
     int family;  /* kernel family chosen (STENCIL_FAMILY_*)                                     */
     int block_x; /* threads along x (streaming family: 128 cells / one 16-byte vector each)      */
     int block_y; /* threads along y (streaming family: block_x * block_y a multiple of 32, at
-                    most 224, or 256 for 3D stars of radius >= 3 with one row per thread)     */
+                    most 224; 3D stars of radius >= 3: 256 with one row per thread, 448 with
+                    two rows per thread in f32 storage)                                       */
     int vec_y;   /* rows per thread (streaming 1, 2 or 4 by stencil; div(k grad u) 1 or 2;
                     general variable-coefficient sweeps 1)                                   */
     int z_chunk; /* planes per CTA (3D); 0 = an equal share per resident CTA (streaming and
-                    div(k grad u)) or whole columns (general variable-coefficient sweeps)     */
+                    div(k grad u)) or whole columns (general variable-coefficient sweeps);
+                    -1 (streaming and div(k grad u)) = every tile column cut into the same
+                    number of near-equal chunks, as many as the resident CTAs allow, so that
+                    the CTAs of neighbouring tiles sweep the same planes at the same time     */
     int fuse;    /* time steps fused per launch                                                 */
     int tile_x;  /* output tile width of fused 2D kernels (0 = default)                         */
     int tile_y;  /* output tile height of fused 2D kernels (0 = default)                        */

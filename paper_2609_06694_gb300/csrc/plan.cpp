@@ -144,11 +144,12 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
         // variable-coefficient kernels: 128-cell tiles, block_y rows of threads with one output
         // row each (div(k grad u): one or two), at most 224 threads, z chunks of z_chunk planes
         // (0: whole columns for the general sweeps, an equal share per resident CTA for
-        // div(k grad u))
+        // div(k grad u); -1, div(k grad u) only: aligned chunks per tile column)
         const bool vy_ok = v.vec_y == 1 || (v.vec_y == 2 && p.kind == STENCIL_DIVKGRAD);
         if (v.family != STENCIL_FAMILY_STREAM || !vy_ok || v.fuse != 1 ||
             v.block_x != (int)(128 / (16 / dtype_size(p.dtype))) || v.block_y < 1 ||
-            v.block_x * v.block_y > 224 || (v.block_x * v.block_y) % 32 != 0 || v.z_chunk < 0)
+            v.block_x * v.block_y > 224 || (v.block_x * v.block_y) % 32 != 0 ||
+            v.z_chunk < (p.kind == STENCIL_DIVKGRAD ? -1 : 0))
             return STENCIL_ERR_BADARG;
         return STENCIL_OK;
     }
@@ -160,7 +161,7 @@ int validate_variant(const stencil_plan_s &p, const stencil_variant &v) {
             return STENCIL_ERR_BADARG;
         if (!stream_vy_compiled(p.ndim, p.shape, p.radius, v.vec_y))
             return STENCIL_ERR_UNSUPPORTED;
-        if (v.z_chunk < 0 || v.fuse != 1) return STENCIL_ERR_BADARG;
+        if (v.z_chunk < -1 || v.fuse != 1) return STENCIL_ERR_BADARG;
         if (v.stages != 0 && (v.stages < 2 || v.stages > 16)) return STENCIL_ERR_BADARG;
         return STENCIL_OK;
     }

@@ -130,6 +130,10 @@ struct RingWork {
     long long w_first, w_end;
     int nzp, tiles_x, tiles_y, TX, TY, RZ;
     int zoff;  // first plane of the z range the sequence covers (nz planes from it)
+    // work > 0: CTA b takes planes [b * work, (b + 1) * work) of the sequence (a range may
+    // continue into the next tile column).  work = -c: every tile column is cut into c chunks
+    // of near-equal length and CTA b takes chunk b % c of column b / c -- no CTA spans two
+    // columns, and the CTAs of neighbouring tiles start at the same planes.
     __device__ __forceinline__ void setup(int tiles_x_, int tiles_y_, int nz, int work, int TX_,
                                           int TY_, int RZ_, int zoff_ = 0) {
         tiles_x = tiles_x_;
@@ -140,8 +144,15 @@ struct RingWork {
         TY = TY_;
         RZ = RZ_;
         const long long total = (long long)tiles_x_ * tiles_y_ * nz;
-        w_first = (long long)blockIdx.x * work;
-        w_end = min(total, w_first + (long long)work);
+        if (work > 0) {
+            w_first = (long long)blockIdx.x * work;
+            w_end = min(total, w_first + (long long)work);
+        } else {
+            const long long c = -(long long)work;
+            const long long col = blockIdx.x / c, k = blockIdx.x % c;
+            w_first = min(total, col * nz + k * nz / c);
+            w_end = min(total, col * nz + (k + 1) * nz / c);
+        }
     }
     __device__ __forceinline__ RingPiece piece_at(long long w) const {
         RingPiece q;

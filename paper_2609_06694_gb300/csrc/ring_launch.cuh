@@ -36,6 +36,14 @@ template <typename T> constexpr CUtensorMapDataType tensor_dtype() {
     else return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
 }
 
+// The column-aligned split of z_chunk == -1 (RingWork with work = -c): c chunks per tile column,
+// as many as the resident CTAs allow (at least one, at most nz); returns -c and the grid.
+inline int ring_column_split(int64_t tiles, int64_t nz, int slots, int64_t *nblocks) {
+    const int64_t c = std::max<int64_t>(1, std::min<int64_t>(nz, slots / std::max<int64_t>(1, tiles)));
+    *nblocks = tiles * c;
+    return -(int)c;
+}
+
 // CTAs of a kernel that can be resident on the whole current device at once (cached per
 // device, kernel and launch shape, under a mutex).
 inline int resident_slots(const void *kern, int threads, size_t smem) {

@@ -35,7 +35,7 @@ int launch_stream_go(const StreamLaunch &L, StreamParams<T> &p,
     // the CTAs that fit on the GPU at once (a multiple of the SM count) and gives each an equal
     // share of the (tile, z) planes.
     const int64_t total = (int64_t)p.tiles_x * p.tiles_y * p.z_cnt;
-    int64_t work;
+    int64_t work, nblocks;
     if (L.z_chunk > 0) {
         work = L.z_chunk;
     } else {
@@ -45,7 +45,13 @@ int launch_stream_go(const StreamLaunch &L, StreamParams<T> &p,
     }
     if (work > INT32_MAX) work = INT32_MAX;
     p.work = (int)work;
-    const int64_t nblocks = (total + work - 1) / work;
+    nblocks = (total + work - 1) / work;
+    // z_chunk == -1: the same number of aligned chunks in every tile column (RingWork)
+    if (L.z_chunk < 0) {
+        const int slots = resident_slots(reinterpret_cast<const void *>(kern), threads, smem);
+        if (slots < 1) return -2;
+        p.work = ring_column_split((int64_t)p.tiles_x * p.tiles_y, p.z_cnt, slots, &nblocks);
+    }
     if (nblocks > INT32_MAX) return -2;
     kern<<<(unsigned)nblocks, dim3(K::BX, by + 32 / K::BX), smem, L.stream>>>(p, cf, ep);
     count_launch();

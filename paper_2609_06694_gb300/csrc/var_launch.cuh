@@ -125,7 +125,13 @@ template <typename T, int NDIM, int VY> int launch_divkgrad_nd(const VarLaunch &
         work = (total + slots - 1) / slots;
     }
     p.work = (int)std::min<int64_t>(work, INT32_MAX);
-    const int64_t nblocks = (total + p.work - 1) / p.work;
+    int64_t nblocks = (total + p.work - 1) / p.work;
+    // z_chunk == -1: the same number of aligned chunks in every tile column (RingWork)
+    if (NDIM == 3 && L.z_chunk < 0) {
+        const int slots = resident_slots(reinterpret_cast<const void *>(kern), threads, smem);
+        if (slots < 1) return -2;
+        p.work = ring_column_split((int64_t)p.tiles_x * p.tiles_y, nz, slots, &nblocks);
+    }
     if (nblocks > INT32_MAX) return -2;
     kern<<<(unsigned)nblocks, dim3(K::BX, by + 32 / K::BX), smem, L.stream>>>(p);
     count_launch();

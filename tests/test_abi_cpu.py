@@ -333,6 +333,25 @@ def test_autotuner_candidates_are_variants_the_library_accepts():
     assert seen > 500
 
 
+def test_column_split_variant_validation():
+    # z_chunk -1 (aligned chunks per tile column) is a work split of the streaming and div(k
+    # grad u) kernels; the general variable-coefficient sweeps and the fused kernels take none
+    p = gs.stencil_plan(3, (64, 64, 64), "star", 4, "const", np.ones(25), "f32", "periodic")
+    v = gs.stencil_plan_get_variant(p)
+    gs.stencil_plan_set_variant(p, **dict(v, z_chunk=-1))
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(p, **dict(v, z_chunk=-2))
+    d = gs.stencil_plan(3, (64, 64, 64), "star", 1, "divkgrad", None, "bf16", "dirichlet")
+    gs.stencil_plan_set_variant(d, **dict(gs.stencil_plan_get_variant(d), z_chunk=-1))
+    w = gs.stencil_plan(3, (64, 64, 64), "star", 1, "var", None, "f32", "dirichlet")
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(w, **dict(gs.stencil_plan_get_variant(w), z_chunk=-1))
+    f = gs.stencil_plan(3, (64, 64, 64), "star", 1, "const", np.ones(7), "f32", "periodic")
+    with pytest.raises(gs.StencilError):
+        gs.stencil_plan_set_variant(f, family=gs.FAMILY_FUSED3D, block_x=32, block_y=4,
+                                    vec_y=2, z_chunk=-1, fuse=2, tile_x=0, tile_y=0, stages=0)
+
+
 def test_streaming_thread_caps():
     # 3D stars of radius >= 3 with one row per thread may take 8 warps of consumers, with two
     # rows per thread in f32 14 (one CTA per SM, taller tiles), every other streaming variant

@@ -194,6 +194,30 @@ def test_periodic_split_copies(dtype, ndim, dims, shape, r, block_y, want):
     assert np.array_equal(inputs.stored_values(ym), got)
 
 
+@pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
+@pytest.mark.parametrize("dtype,shape,r,block_y,vec_y", [
+    ("f32", "star", 4, 14, 2), ("f32", "star", 4, 7, 2), ("f32", "box", 1, 4, 2),
+    ("bf16", "star", 2, 8, 2), ("f16", "diamond", 1, 14, 1)])
+def test_column_aligned_split(bc, dtype, shape, r, block_y, vec_y):
+    # z_chunk -1: every tile column cut into the same number of chunks (as many as the
+    # resident CTAs allow, here one to several per column); the same bits as one equal share
+    # per CTA and as 5-plane chunks, and the oracle's values
+    dims = (37, 92, 264)
+    offs = oracle.offsets(3, shape, r)
+    c = seeded_weights(81, len(offs))
+    plan = gs.stencil_plan(3, dims, shape, r, "const", c, dtype, bc)
+    bx = 32 if dtype == "f32" else 16
+    x, x64 = make_input(82, dims, dtype)
+    outs = []
+    for zc in (-1, 0, 5):
+        gs.stencil_plan_set_variant(plan, family=1, block_x=bx, block_y=block_y, vec_y=vec_y,
+                                    z_chunk=zc, stages=0, fuse=1)
+        outs.append(gpu_apply(plan, x))
+    assert relerr(outs[0], oracle.sweep_const(x64, offs, c, bc)) < TOL[dtype]
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("shape,r,block_y,vec_y", [("star", 4, 8, 1), ("star", 4, 7, 2),
                                                    ("star", 4, 4, 2), ("star", 2, 3, 2),

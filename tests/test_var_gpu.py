@@ -84,8 +84,9 @@ def test_var_rejects_missing_arrays_and_unsupported_sets():
 @pytest.mark.parametrize("bc", ["dirichlet", "periodic"])
 def test_divkgrad_work_splits(dtype, bc):
     # one equal share of the (tile, z) planes per resident CTA (z_chunk 0: a CTA's planes span
-    # several tiles), short chunks that end mid-column, several tile heights, one and two rows
-    # per thread: every split gives the same bits and matches the oracle
+    # several tiles), aligned chunks per tile column (z_chunk -1), short chunks that end
+    # mid-column, several tile heights, one and two rows per thread: every split gives the
+    # same bits and matches the oracle
     dims = (23, 45, 264)
     plan = gs.stencil_plan(3, dims, "star", 1, "divkgrad", None, dtype, bc)
     k = inputs.to_storage(inputs.lognormal_k(3012, dims), dtype)
@@ -96,7 +97,7 @@ def test_divkgrad_work_splits(dtype, bc):
     first = None
     f = 1 if bx == 32 else 2  # 16-bit rows of 128 cells take 16 threads: twice the rows
     for by, vy, zc in ((4, 1, 0), (2 * f, 1, 0), (7 * f, 1, 5), (f, 1, 9), (4 * f, 2, 16),
-                       (7 * f, 2, 0), (f, 2, 3)):
+                       (7 * f, 2, 0), (f, 2, 3), (4 * f, 2, -1), (f, 1, -1)):
         gs.stencil_plan_set_variant(plan, **dict(base, block_y=by, vec_y=vy, z_chunk=zc,
                                                  stages=0))
         y = torch.empty_like(u, device="cuda")
