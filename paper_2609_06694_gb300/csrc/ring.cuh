@@ -148,10 +148,14 @@ struct RingWork {
             w_first = (long long)blockIdx.x * work;
             w_end = min(total, w_first + (long long)work);
         } else {
-            const long long c = -(long long)work;
-            const long long col = blockIdx.x / c, k = blockIdx.x % c;
-            w_first = min(total, col * nz + k * nz / c);
-            w_end = min(total, col * nz + (k + 1) * nz / c);
+            // chunk k of a column starts at k * q + min(k, r) (q = nz / c, r = nz % c: the
+            // first r chunks take one plane more); 32-bit divisions only
+            const unsigned c = (unsigned)(-work), b = blockIdx.x;
+            const unsigned col = b / c, k = b - col * c;
+            const unsigned q = (unsigned)nz / c, r = (unsigned)nz - q * c;
+            const long long base = (long long)col * nz;
+            w_first = min(total, base + (long long)(k * q + min(k, r)));
+            w_end = min(total, base + (long long)((k + 1) * q + min(k + 1, r)));
         }
     }
     __device__ __forceinline__ RingPiece piece_at(long long w) const {
@@ -243,7 +247,9 @@ __device__ __forceinline__ int ring_side_bits(bool use_side, int x0, int y0, int
 //  mode 0: element copies (rows not 16-byte aligned).
 // Field f of a slot starts f * field_bytes into it; rows are PITCH elements apart and the
 // tile's column 0 sits A elements into a row.
-template <typename T, int NF, int NDIM, int R, int A, int PITCH, int TX>
+// YSPLIT: mode 6 is compiled in (the plain periodic streaming sweep); other kernels patch the
+// wrapped rows (mode 4) and keep the producer's registers -- and their occupancy -- as they were.
+template <typename T, int NF, int NDIM, int R, int A, int PITCH, int TX, bool YSPLIT = false>
 __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, NF> &src,
                                              const RingWork &wk, int *err, int lane) {
     constexpr int ES = (int)sizeof(T);
@@ -279,13 +285,13 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
         const int nrow_oob = lo_row + min(rows - hi_row, R);
         const int nwc = lo_chk + min(CPR - hi_chk, 1);
         const int npatch = nrow_oob * CPR + (hi_row - lo_row) * nwc;
-        const int yk = NF == 1 ? ring_ysplit(src.ysplit, q.y0, ny, wk.TY, R) : 0;
+        const int yk = (YSPLIT && NF == 1) ? ring_ysplit(src.ysplit, q.y0, ny, wk.TY, R) : 0;
         const int sbits = ring_side_bits(src.use_side, q.x0, q.y0, nx, ny, TX, wk.TY, R, A, yk);
         const bool x_inside = q.x0 >= A && q.x0 + TX + A <= nx;
         int mode;
         if (!src.use_tma) mode = src.aligned ? 1 : 0;
         else if (!periodic || npatch == 0) mode = 2;
-        else if (yk != 0 && (x_inside || sbits != 0)) mode = 6;
+        else if (YSPLIT && yk != 0 && (x_inside || sbits != 0)) mode = 6;
         else if (sbits != 0) mode = 5;
         else if (npatch <= kMaxPatches && hi_row >= lo_row) mode = 4;
         else mode = 3;
@@ -362,7 +368,7 @@ __device__ __forceinline__ void ring_produce(const Ring &g, const RingSource<T, 
                     mbar_arrive(bar);
                 }
                 if (mode == 4) ++unpub;
-            } else if (mode == 6) {
+            } else if (YSPLIT && mode == 6) {
                 // top: wrapped rows from ny - R into slot rows [0, R), grid rows from 0 into
                 // [R, rows); bottom: grid rows from y0 - R into [0, hb + R), wrapped rows from 0
                 // into [hb + R, hb + 2R); the side arrays alike.  Every split lies on a 128-byte

@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(
         src.rows = rows;
         src.ymaps = p.ymap;
         src.ysplit = p.ysplit;
-        ring_produce<T, 1, NDIM, R, A, PITCH, TX>(g, src, wk, p.err, lane);
+        // the y-split copies only where a split can land on 128 bytes at the top (radius 4)
+        ring_produce<T, 1, NDIM, R, A, PITCH, TX, SIDE && R == 4>(g, src, wk, p.err, lane);
         return;
     }
 

@@ -110,9 +110,11 @@ int launch_stream_t(const StreamLaunch &L,
     // periodic tile rows at the y ends: their wrapped rows by split tensor copies (ring.cuh,
     // mode 6) where each split lands on a 128-byte boundary of the slot (and of the side
     // arrays, 32-byte rows), the top row of tiles needs no bottom wrap (ny >= TY + 2R) and
-    // only the last row of tiles wraps at the bottom (its hb output rows >= R)
+    // only the last row of tiles wraps at the bottom (its hb output rows >= R).  Compiled
+    // for radius 4 only (the one radius whose top split lands on 128 bytes: R rows of 16-byte
+    // chunks); the smaller kernels keep the producer's registers.
     p.ysplit = 0;
-    if (p.use_tma && L.periodic && p.tiles_y >= 2 && ny >= TY + 2 * R) {
+    if (R == 4 && p.use_tma && L.periodic && p.tiles_y >= 2 && ny >= TY + 2 * R) {
         const int64_t hb = ny - (int64_t)(p.tiles_y - 1) * TY;
         const int64_t row_bytes = (int64_t)K::PITCH * (int64_t)sizeof(T);
         auto fits = [&](int64_t split) {
@@ -133,11 +135,13 @@ int launch_stream_t(const StreamLaunch &L,
     ConstCoeffs<NPTS> cf;
     for (int i = 0; i < NPTS; ++i) cf.c[i] = L.coeffs[i];
 
-    // the side-array kernel only where side chunks may be taken (plain periodic sweeps)
+    // the side-array kernel (with the y-split copies) only where side chunks may be taken
+    // (plain periodic sweeps)
     if constexpr (std::is_same<EPI, PlainStoreEpi>::value) {
         if (p.use_side) return launch_stream_go<T, NDIM, SHAPE, R, VY, QM, EPI, true>(L, p, cf, ep);
     }
     p.use_side = 0;
+    p.ysplit = 0;
     return launch_stream_go<T, NDIM, SHAPE, R, VY, QM, EPI, false>(L, p, cf, ep);
 }
 

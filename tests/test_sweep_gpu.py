@@ -135,11 +135,12 @@ def test_periodic_whole_tile_widths(dtype, shape, r):
 
 def _split_rows(ny, ty, r, pitch_bytes):
     """Which y-end tile rows of a periodic grid take split tensor copies (the rows inside the
-    grid and the R wrapped rows as two copies, at 128-byte boundaries of the slot): the same
-    rule as the library's launcher, restated for the test's coverage checks."""
+    grid and the R wrapped rows as two copies, at 128-byte boundaries of the slot; compiled for
+    radius 4): the same rule as the library's launcher, restated for the test's coverage
+    checks."""
     tiles_y = -(-ny // ty)
     hb = ny - (tiles_y - 1) * ty
-    if tiles_y < 2 or ny < ty + 2 * r or hb < r:
+    if r != 4 or tiles_y < 2 or ny < ty + 2 * r or hb < r:
         return set()
     out = set()
     if (r * pitch_bytes) % 128 == 0:
@@ -156,7 +157,7 @@ def _split_rows(ny, ty, r, pitch_bytes):
     (3, (10, 134, 128), "star", 4, 7, ({"top", "bottom"}, {"top"})),  # one tile column
     (3, (12, 140, 256), "star", 4, 7, ({"top"}, {"top", "bottom"})),
     (3, (9, 92, 256), "star", 4, 14, ({"top", "bottom"}, None)),      # 28-row f32 tiles
-    (3, (11, 70, 256), "box", 2, 4, ({"bottom"}, {"bottom"})),        # R = 2
+    (3, (11, 70, 256), "box", 2, 4, (set(), set())),                  # R = 2: patched
     (2, (134, 384), "star", 4, 7, ({"top", "bottom"}, {"top"})),
 ])
 def test_periodic_split_copies(dtype, ndim, dims, shape, r, block_y, want):
