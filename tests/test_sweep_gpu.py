@@ -246,13 +246,14 @@ def test_periodic_side_chunks(dtype, shape, r, block_y, vec_y):
         assert relerr(got, oracle.sweep_const(x64, offs, c, "periodic")) < TOL[dtype], (ndim, dims)
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-@pytest.mark.parametrize("steps", [1, 2, 3])
+@pytest.mark.parametrize("dtype,steps", [("f32", 1), ("f32", 2), ("f32", 3), ("f32", 8),
+                                         ("bf16", 1), ("bf16", 2), ("bf16", 3)])
 def test_apply_host_buffers(dtype, steps):
     # stencil_apply_host: 3D grids deep enough for the z-slab pipeline (copies in and out
-    # overlapping the sweeps; a periodic grid sweeps its first slab last), a shallow one and a
-    # 2D one on the simple path; pinned and pageable host buffers.  Bit for bit equal to the
-    # device-buffer path, and within tolerance of the oracle.
+    # overlapping the sweeps; several sweeps as a wavefront over z whose periodic ends follow
+    # the bands), a shallow one and a 2D one on the simple path; pinned and pageable host
+    # buffers.  Bit for bit equal to the device-buffer path, and within tolerance of the
+    # oracle.
     cases = [(3, (70, 40, 256), "star", 4, "periodic"), (3, (130, 33, 128), "box", 1, "dirichlet"),
              (3, (64, 20, 130), "diamond", 2, "periodic"), (3, (9, 20, 64), "star", 2, "periodic"),
              (2, (90, 300), "box", 2, "periodic")]
