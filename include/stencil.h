@@ -163,12 +163,14 @@ int stencil_apply_adjoint_var(stencil_handle h, const void *in,
 /* stencil_apply_host -- stencil_apply on HOST buffers: copies `in_host` to a device staging
  * buffer, sweeps, and copies the result to `out_host`, then synchronises `stream`; the result
  * is bit for bit that of stencil_apply.  3D grids on the streaming kernel are pipelined over
- * z slabs: input slabs are copied in on a stream of the plan's, each slab of output planes of
- * the first sweep starts as soon as the input planes it reads have landed, and the output
- * slabs of the last sweep are copied out on a second stream of the plan's as they finish, so
- * both copy directions overlap the sweeps and each other (work queued on `stream` before the
- * call is ordered before the copies).  Pinned host memory gives full copy bandwidth.  The
- * staging buffers, streams and events are created on first use and kept by the plan. */
+ * z slabs: input slabs are copied in on a stream of the plan's; sweep t of the output planes
+ * up to A - t*radius runs as soon as input planes [0, A) have landed (a wavefront over z; on
+ * a periodic grid the planes near either end, which read wrapped planes, follow once the
+ * input is complete), and the finished planes of the last sweep are copied out on a second
+ * stream of the plan's, so both copy directions overlap the sweeps and each other (work
+ * queued on `stream` before the call is ordered before the copies).  Pinned host memory gives
+ * full copy bandwidth.  The staging buffers, streams and events are created on first use and
+ * kept by the plan. */
 int stencil_apply_host(stencil_handle h, const void *in_host, void *out_host, int steps,
                        void *stream);
 
