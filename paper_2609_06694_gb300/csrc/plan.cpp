@@ -16,6 +16,7 @@
 #include "../../include/stencil.h"
 #include "internal.h"
 #include "plan_internal.h"
+#include "wavefront.h"
 
 namespace gst {
 
@@ -344,78 +345,36 @@ using namespace gst;
 // directions overlap the sweeps and each other.  Slab k reads input planes up to R beyond
 // its end, so it waits for input slab k + 1; on a periodic grid slab 0 also reads the last
 // planes, so it is swept last.
-// Several sweeps of stencil_apply_host as a wavefront over z (the input copied in on s_in
-// as in the single sweep, slab k recorded by ev_in[k]): sweep t of planes [a, b) reads sweep
-// t - 1 on [a - R, b + R), so once the input planes [0, A) have landed, sweep 1 can run up to
-// A - R, sweep 2 up to A - 2R, ..., and the finished planes of the last sweep go out on s_out
-// while later input is still coming in.  Each sweep t keeps a frontier F[t]; a zero-Dirichlet
-// grid fills [0, F[t]) and reaches nz with the last input slab.  On a periodic grid the planes
-// near either end of sweep t read wrapped planes of sweep t - 1: its band is [tR, nz - tR),
-// and [F[t], nz) and [0, tR) follow once every band is complete, sweep by sweep.  All sweeps
-// run in order on the caller's stream, and the sweeps alternate between the scratch grid and
-// stage_out (the last one writes stage_out), so a sweep never overwrites planes that the
-// sweep before it still has to read: F[t + 2] <= F[t + 1] - R.
+// Several sweeps of stencil_apply_host: the wavefront over z of wavefront.h, the input copied
+// in on s_in as in the single sweep (slab k recorded by ev_in[k]), the sweeps in order on the
+// caller's stream, alternating between the scratch grid and stage_out (the last one writes
+// stage_out), the finished planes of the last sweep out on s_out.
 static int host_wavefront(stencil_plan_s &h, char *hout, int steps, const int64_t *zb,
                           int nslab, cudaStream_t s) {
     constexpr int kMax = stencil_plan_s::kMaxSlabs;
-    const int64_t nz = h.dims[0];
     const size_t plane = (size_t)h.dims[1] * h.dims[2] * dtype_size(h.dtype);
-    const int64_t R = h.radius;
-    const bool periodic = h.boundary == STENCIL_PERIODIC;
     const char *dout = static_cast<const char *>(h.stage_out);
     auto check = [](cudaError_t e) { return e == cudaSuccess; };
     auto dst_of = [&](int t) -> void * { return ((steps - t) % 2 == 0) ? h.stage_out : h.scratch; };
     auto src_of = [&](int t) -> const void * { return t == 1 ? h.stage_in : dst_of(t - 1); };
-    // sweep t on output planes [a, b)
-    auto sweep = [&](int t, int64_t a, int64_t b) -> int {
-        if (b <= a) return STENCIL_OK;
-        return launch_group(h, h.cf.data(), src_of(t), dst_of(t), 1, s, a, b);
-    };
     int nev = 0;
-    // planes [a, b) of the last sweep out to the host once the launches so far are done
-    auto copy_out = [&](int64_t a, int64_t b) -> int {
-        if (b <= a) return STENCIL_OK;
-        cudaEvent_t e = h.ev_out[nev++ % kMax];
-        if (!check(cudaEventRecord(e, s)) || !check(cudaStreamWaitEvent(h.s_out, e, 0)) ||
-            !check(cudaMemcpyAsync(hout + (size_t)a * plane, dout + (size_t)a * plane,
-                                   (size_t)(b - a) * plane, cudaMemcpyDeviceToHost, h.s_out)))
-            return STENCIL_ERR_CUDA;
-        return STENCIL_OK;
-    };
-    std::vector<int64_t> lo(steps + 1), hi(steps + 1), F(steps + 1);
-    for (int t = 1; t <= steps; ++t) {
-        lo[t] = periodic ? std::min<int64_t>(t * R, nz) : 0;
-        hi[t] = periodic ? std::max<int64_t>(lo[t], nz - t * R) : nz;
-        F[t] = lo[t];
-    }
-    int64_t sent = lo[steps];  // the last sweep's planes [lo, sent) are on their way out
-    for (int k = 0; k < nslab; ++k) {
-        if (!check(cudaStreamWaitEvent(s, h.ev_in[k], 0))) return STENCIL_ERR_CUDA;
-        int64_t avail = zb[k + 1];  // frontier of the values the next sweep reads
-        for (int t = 1; t <= steps; ++t) {
-            const int64_t target = periodic ? std::min(hi[t], std::max(lo[t], avail - R))
-                                            : (avail >= nz ? nz : std::max<int64_t>(0, avail - R));
-            if (target > F[t]) {
-                const int rc = sweep(t, F[t], target);
-                if (rc) return rc;
-                F[t] = target;
-            }
-            avail = F[t];
-        }
-        const int rc = copy_out(sent, F[steps]);
-        if (rc) return rc;
-        sent = std::max(sent, F[steps]);
-    }
-    if (periodic) {
-        for (int t = 1; t <= steps; ++t) {
-            int rc = sweep(t, F[t], nz);
-            if (!rc) rc = sweep(t, 0, lo[t]);
-            if (rc) return rc;
-        }
-        int rc = copy_out(sent, nz);
-        if (!rc) rc = copy_out(0, lo[steps]);
-        if (rc) return rc;
-    }
+    const int rc = wavefront_schedule(
+        h.dims[0], h.radius, h.boundary == STENCIL_PERIODIC, steps, zb, nslab,
+        [&](int kind, int slab, int t, int64_t a, int64_t b) -> int {
+            if (kind == kWaveWaitInput)
+                return check(cudaStreamWaitEvent(s, h.ev_in[slab], 0)) ? STENCIL_OK
+                                                                       : STENCIL_ERR_CUDA;
+            if (kind == kWaveSweep)
+                return launch_group(h, h.cf.data(), src_of(t), dst_of(t), 1, s, a, b);
+            // the last sweep's planes [a, b) out to the host once the launches so far are done
+            cudaEvent_t e = h.ev_out[nev++ % kMax];
+            if (!check(cudaEventRecord(e, s)) || !check(cudaStreamWaitEvent(h.s_out, e, 0)) ||
+                !check(cudaMemcpyAsync(hout + (size_t)a * plane, dout + (size_t)a * plane,
+                                       (size_t)(b - a) * plane, cudaMemcpyDeviceToHost, h.s_out)))
+                return STENCIL_ERR_CUDA;
+            return STENCIL_OK;
+        });
+    if (rc) return rc;
     if (!check(cudaEventRecord(h.ev_done, h.s_out)) || !check(cudaStreamWaitEvent(s, h.ev_done, 0)))
         return STENCIL_ERR_CUDA;
     return cuda_status(cudaStreamSynchronize(s));
