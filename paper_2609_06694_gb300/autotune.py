@@ -185,6 +185,21 @@ def _problem(ndim, dims, shape, radius, dtype, bc, kind):
     return plan, (lambda p, n: gs.stencil_apply(p, x, y, n)), 2
 
 
+def rank_timings(ev):
+    """Timed candidates fastest first; ties (within 1% of the fastest) go to the
+    column-aligned z split (z_chunk -1): a map entry serves every grid of its size class, and
+    that split keeps the CTAs of neighbouring tiles in step whatever the number of tiles (on a
+    384^3 grid the equal share per CTA ran 9-12% slower for the radius-4 star; they tie at
+    512^3)."""
+    ev = sorted(ev, key=lambda e: e["ms"])
+    if ev:
+        tied = [e for e in ev if e["ms"] <= ev[0]["ms"] * 1.01 and e["variant"]["z_chunk"] == -1]
+        if tied:
+            ev.remove(tied[0])
+            ev.insert(0, tied[0])
+    return ev
+
+
 def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=print,
              kind="const"):
     """Time every candidate on `dims`; returns (best_variant, evidence list, candidates timed).
@@ -215,16 +230,7 @@ def tune_key(ndim, dims, shape, radius, dtype, bc, steps=1, quick=False, log=pri
         gbs = bytes_per_cell * es * cells * steps / (ms * 1e-3) / 1e9
         ev.append({"variant": v, "ms": round(ms, 5), "steps": steps, "alg_GBps": round(gbs, 1),
                    "frac_hbm": round(gbs / peak, 4)})
-    ev.sort(key=lambda e: e["ms"])
-    # Ties (within 1% of the fastest) go to the column-aligned z split (z_chunk -1): a map
-    # entry serves every grid of its size class, and that split keeps the CTAs of
-    # neighbouring tiles in step whatever the number of tiles (on a 384^3 grid the equal
-    # share per CTA ran 9-12% slower for the radius-4 star, ties at 512^3).
-    if ev:
-        tied = [e for e in ev if e["ms"] <= ev[0]["ms"] * 1.01 and e["variant"]["z_chunk"] == -1]
-        if tied:
-            ev.remove(tied[0])
-            ev.insert(0, tied[0])
+    ev = rank_timings(ev)
     n_timed = len(ev)
     # the evidence keeps the ten fastest and, behind them, the fastest of every other kernel
     # family (so a family that lost is still on record with its best time)

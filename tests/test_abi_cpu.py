@@ -303,6 +303,23 @@ def _plan_for(ndim, dims, shape, r, dtype, bc, kind):
                            np.ones(len(oracle.offsets(ndim, shape, r))), dtype, bc)
 
 
+def test_autotuner_ranking_prefers_the_aligned_split_on_ties():
+    from paper_2609_06694_gb300 import autotune
+
+    def ev(ms, zc, by=14):
+        return {"ms": ms, "variant": {"z_chunk": zc, "block_y": by}}
+
+    # within 1% of the fastest: the column-aligned split wins
+    r = autotune.rank_timings([ev(0.2000, 0), ev(0.2015, -1), ev(0.2100, 64)])
+    assert r[0]["variant"]["z_chunk"] == -1 and [e["ms"] for e in r[1:]] == [0.2000, 0.2100]
+    # beyond 1%: the fastest stays first
+    r = autotune.rank_timings([ev(0.2030, -1), ev(0.2000, 0)])
+    assert r[0]["variant"]["z_chunk"] == 0
+    # no aligned candidate: plain order by time
+    assert [e["ms"] for e in autotune.rank_timings([ev(0.3, 0), ev(0.1, 64)])] == [0.1, 0.3]
+    assert autotune.rank_timings([]) == []
+
+
 def test_autotuner_candidates_are_variants_the_library_accepts():
     # every candidate the tuner would time is a variant the plan validation accepts, so a
     # tuning run never spends its time on launches the library refuses (host logic only)
