@@ -70,3 +70,10 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with contextlib.redirect_stdout(out):
         bench.bench_reference(types.SimpleNamespace(steps=1, warmup=1, gpus=2))
     assert out.getvalue() == ""
+
+
+def test_committed_profile_matches_the_kernel_sources():
+    # the bench line's roofline.traffic comes from the committed ncu summary of its dominant
+    # kernel only while stream.cuh and ring.cuh hash as they did when it was captured: a change
+    # to either file needs a new capture, not an edited hash
+    assert bench.traffic_from_profile("stream_sweep_star_r4_512") is not None
