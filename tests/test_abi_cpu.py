@@ -485,3 +485,33 @@ def test_tensor_variant_validation():
         with pytest.raises(gs.StencilError) as e:
             gs.stencil_plan_set_variant(p, **kw)
         assert e.value.code == -1
+
+
+def test_every_map_line_is_a_recorded_autotuner_winner():
+    # dispatch_map.txt holds no hand-set line: every line is the fastest candidate of its key in
+    # dispatch_evidence.json (the autotuner's record), and every key carries the winner's ncu
+    # DRAM counters
+    import json
+    pkg = os.path.join(ROOT, "paper_2609_06694_gb300")
+    ev = json.load(open(os.path.join(pkg, "dispatch_evidence.json")))["keys"]
+    names = ["family", "block_x", "block_y", "vec_y", "z_chunk", "fuse", "tile_x", "tile_y",
+             "stages"]
+    want = {}
+    for e in ev:
+        k, best = e["key"], e["fastest"][0]
+        assert e.get("winner_ncu") and e["winner_ncu"]["dram_bytes_read"] > 0, k
+        if "batch" in k:
+            s = best["shape"]
+            want[f"batch {api.DTYPES[k['batch']]}"] = [s["tile_y"], s["tile_x"], s["fuse"]]
+        else:
+            key = [k["ndim"], api.SHAPES[k["shape"]], k["radius"], api.DTYPES[k["dtype"]],
+                   api.BOUNDARIES[k["boundary"]], api.KINDS[k["kind"]], k["size_class"],
+                   k["geometry"]]
+            want[" ".join(map(str, key))] = [best["variant"].get(n, 0) for n in names]
+    lines = [ln.split("#")[0].strip() for ln in open(os.path.join(pkg, "dispatch_map.txt"))]
+    lines = [ln for ln in lines if ln]
+    assert len(lines) == len(want)
+    for ln in lines:
+        key, val = (part.strip() for part in ln.split(":"))
+        assert key in want, ln
+        assert [int(v) for v in val.split()] == want[key], ln
